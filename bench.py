@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the HELIOS-K hot path on GB300: one step = one (T, P)
+condition through the whole path -- line preparation, Voigt opacity on the
+grid (Sec. 2.3-2.5) and the per-bin k-distribution tables (sort + Chebyshev
+fit, Sec. 2.6) -- on the "medium" synthetic workload: 1e5 lines over
+0-30000 cm^-1, 3e6-point grid at 0.01 cm^-1, cutoff 100 cm^-1, 300 bins x 20
+coefficients, T = 1500 K, P = 1 atm, 18 amu.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is Voigt evaluations per second of the whole
+step with the line list resident in HBM; `e2e` is the same metric through the
+C ABI from pinned host buffers (upload, opacity, tables back to the host).
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.  Under torchrun each rank
+runs its own condition (weak scaling, no data-path collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Voigt evals/s and opacity+k-table time/(T,P) vs plain FP64 GPU at stated rel err"
+UNIT = "Voigt evals/s"
+WORKLOAD = "medium"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic floating-point operations per evaluation (add/sub/mul/div = 1,
+# fma = 2), per method, as written in the kernels' formulas:
+#   GH1  u, r^2, one division, accumulate                     -> 6
+#   GH3  u, r^2, u-+t, d1, d2, d1+d2, d1 d2, num, den, /, *, + -> 19
+#   916  33 per evaluation + 10 per series term
+FLOPS_GH1, FLOPS_GH3, FLOPS_916_EVAL, FLOPS_916_TERM = 6, 19, 33, 10
+# FP64 pipe of GB300: 2 FP64 FMA / clock / SM (1.25 TFLOP/s nominal at the
+# 2.07 GHz maximum clock over 152 SMs).
+FP64_FMA_PER_CLK_SM = 2
+
+
+def workload_desc(w):
+    return ("medium: %d lines over 0-30000 cm^-1, %d-point grid at %g cm^-1, cutoff %g cm^-1, "
+            "%d k-bins x %d Chebyshev coefficients, T=%g K, P=%g atm, %g amu"
+            % (w["nlines"], w["ngrid"], w["dnu"], w["cut"][1], w["nbins"], w["ncheb"], w["T"][0],
+               w["P_atm"][0], w["mass"]))
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def traffic_from_profile(kernel_src, profile_txt):
+    """Per-launch DRAM bytes recorded by an ncu capture, if the kernel source
+    is unchanged since (hash recorded in the summary)."""
+    try:
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        with open(profile_txt) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != h:
+            return None
+        return float(vals["dram_bytes_per_launch_full_workload"])
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------- oracle --
+def oracle_sample(w, lines, target_s, nthreads):
+    """Time the FP64 oracle on a contiguous slab of k-bins (all their lines):
+    opacity on the slab's grid + sort + Chebyshev fit.  Returns
+    (evals, seconds, nbins_used)."""
+    import oracle
+    nb = w["ngrid"] // w["nbins"]
+
+    def run(nbins_s, b0):
+        cond = oracle.Condition(w["T"][0], w["P_atm"][0], w["mass"],
+                                w["nu_min"] + b0 * nb * w["dnu"], w["dnu"], nbins_s * nb,
+                                oracle.CUT_ABS, w["cut"][1])
+        t = time.perf_counter()
+        k, ev, _ = oracle.opacity(lines, cond, nthreads=nthreads)
+        oracle.kdist(k, nbins_s, w["ncheb"])
+        return ev, time.perf_counter() - t
+
+    b0 = w["nbins"] // 2
+    ev, dt = run(1, b0)
+    nbins_s = max(1, min(w["nbins"] - b0, int(target_s / max(dt, 1e-3))))
+    if nbins_s > 1:
+        ev, dt = run(nbins_s, b0)
+    return ev, dt, nbins_s
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1503_03806_gb300 import synth
+    import oracle
+    oracle.lib()
+    w = synth.WORKLOADS[WORKLOAD]
+    lines = synth.workload_lines(WORKLOAD)
+    cores = os.cpu_count() or 1
+    # size one step at ~1/(K+W) of a ~60 s budget
+    per_step = max(2.0, 60.0 / (args.steps + args.warmup))
+    ev1, dt1, nbs = oracle_sample(w, lines, per_step, cores)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(w, lines, per_step, cores)
+    evs, dts = [], []
+    for _ in range(args.steps):
+        ev, dt, nbs = oracle_sample(w, lines, per_step, cores)
+        evs.append(ev)
+        dts.append(dt)
+    value = sum(evs) / sum(dts)
+    sample = "%d contiguous k-bins (%d grid points, all overlapping lines) per step" % (
+        nbs, nbs * (w["ngrid"] // w["nbins"]))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": workload_desc(w), "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, local_rank, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1503_03806_gb300 import helk, synth
+
+    w = synth.WORKLOADS[WORKLOAD]
+    T = w["T"][0] if world == 1 else float(np.linspace(500.0, 3000.0, world)[rank])
+    P, mass, cut = w["P_atm"][0], w["mass"], w["cut"]
+    grid = (w["nu_min"], w["dnu"], w["ngrid"])
+    nbins, ncheb = w["nbins"], w["ncheb"]
+    lines = synth.workload_lines(WORKLOAD)
+    prec = helk.HELK_PREC_F64
+
+    ctx = helk.Context(local_rank)
+    ctx.upload(lines)
+    kappa = torch.empty(grid[2], dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # work of one step (exact counts from the counting variant of the kernel)
+    ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec, count_regions=True)
+    evals, reg = ctx.stats(with_regions=True)
+    flops = (reg[2] * FLOPS_GH1 + reg[1] * FLOPS_GH3 + reg[0] * FLOPS_916_EVAL
+             + reg[3] * FLOPS_916_TERM)
+
+    def step():
+        ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec)
+        ctx.kdist(kappa, nbins, ncheb)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    with Clocks(local_rank) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()                      # L2 flush, outside the timed events
+            starts[i].record()
+            step()
+            ends[i].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    stage = ctx.stage_times()
+    ctx.set_profiling(False)
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * evals / (ms_step * 1e-3)
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in lines.items()}
+        h2d = sum(v.numel() * 8 for v in pinned.values())
+        coef_h = np.empty((nbins, ncheb))
+        d2h = coef_h.nbytes + nbins * 8
+
+        def e2e_step():
+            ctx.upload(pinned)
+            ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec)
+            ctx.kdist(kappa, nbins, ncheb, on_host=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t1)
+        e2e_s = sum(tt) / len(tt)
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak64 = FP64_FMA_PER_CLK_SM * 2 * nsm * max_mhz * 1e6 / 1e12
+    voigt_ms, voigt_n = stage["voigt"]
+    voigt_avg_s = voigt_ms / max(1, voigt_n) * 1e-3
+    achieved = flops / voigt_avg_s / 1e12
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_1503_03806_gb300", "csrc", "k_voigt.cu"),
+                                   os.path.join(ROOT, "profiles", "voigt_f64_medium.txt"))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": traffic, "kernel": "k_voigt_f64",
+                "peak_basis": "FP64 pipe, %d FMA/clk/SM x %d SMs x %.0f MHz (derived)"
+                              % (FP64_FMA_PER_CLK_SM, nsm, max_mhz),
+                "flops_per_launch": flops}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / (peak64 * clocks["sm_mhz"] / max_mhz)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ev_c, dt_c, nbs = oracle_sample(w, lines, 10.0, cores)
+        cpu = {"value": ev_c / dt_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d contiguous k-bins (%d grid points, all overlapping lines): opacity + "
+                         "sort + fit, %.1f s" % (nbs, nbs * (grid[2] // nbins), dt_c)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": workload_desc(w), "precision": "fp64",
+                          "l2": "flushed between steps (256 MB write)",
+                          "evals_per_step": evals,
+                          "evals_by_method": {"alg916": int(reg[0]), "gh3": int(reg[1]),
+                                              "gh1": int(reg[2])}},
+               "stages_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
+               "wall_s_timed": wall, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clocks, "gpu_launches": 4 * args.steps}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * helk.h -- C ABI of the GB300 (sm_103a) HELIOS-K hot path.
+ *
+ * Method: Grimm & Heng 2015, "HELIOS-K: an ultrafast, open-source opacity
+ * calculator for radiative transfer" (arXiv:1503.03806).
+ *   Opacity  kappa(nu) = sum_lines S Phi(nu)              Sec. 2.3 (kappa = S Phi)
+ *   Voigt    Phi = sqrt(ln2/pi) H_V(a,u) / Gamma_D        Sec. 2.4
+ *   H_V by Algorithm 916 for a^2+u^2 < 100, 3-node Gauss-Hermite for
+ *   100 <= a^2+u^2 < 1e6 and 1-node Gauss-Hermite beyond  Sec. 2.5
+ *   line-wing cutoff                                       Sec. 2.5
+ *   k-distribution: per-bin sort, k(g), Chebyshev fit      Sec. 2.2, 2.6
+ *   transmission T(m) = int_0^1 exp(-k(g) m) dg            Sec. 2.1
+ *
+ * Conventions common to every entry point:
+ *  - All entry points return helk_status; none aborts.  On failure the
+ *    context keeps a message readable with helk_last_error().
+ *  - Work is enqueued on the context's CUDA stream and the call returns
+ *    before it finishes, unless stated otherwise.  Errors raised by kernels
+ *    (for example a bounded wait that gave up: HELK_ERR_TIMEOUT) are reported
+ *    by the next helk_sync() or by any call that reads results to the host.
+ *  - "device pointer" means memory of the context's device (e.g. a torch
+ *    tensor's data_ptr()); the caller owns it and keeps it alive until the
+ *    work that uses it has completed.  Host pointers are only read during
+ *    the call (data are copied before it returns).
+ *  - Units: wavenumber cm^-1, T in K, P in atm (P0 = 1 atm), mass in amu,
+ *    S in cm/molecule; opacities are cross-sections in cm^2/molecule.
+ *  - Grid sizes are limited to 2^31 - 1 points, line lists to 2^31 - 1
+ *    lines.
+ */
+#ifndef HELK_H
+#define HELK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helk_ctx helk_ctx;
+
+typedef enum {
+    HELK_OK = 0,
+    HELK_ERR_INVALID_ARG = -1, /* bad value, size or pointer               */
+    HELK_ERR_OOM = -2,         /* device or host allocation failed         */
+    HELK_ERR_CUDA = -3,        /* CUDA runtime error (text in last_error)  */
+    HELK_ERR_STATE = -4,       /* call order (e.g. opacity before upload)  */
+    HELK_ERR_TIMEOUT = -5,     /* a kernel's bounded wait gave up          */
+    HELK_ERR_UNSUPPORTED = -6  /* option not available in this build       */
+} helk_status;
+
+/* Uniform wavenumber grid nu_i = nu_min + i * dnu, i = 0 .. n-1
+ * (Sec. 2.2: equal intervals delta x).  dnu > 0, 0 < n < 2^31. */
+typedef struct {
+    double nu_min;
+    double dnu;
+    int64_t n;
+} helk_grid;
+
+/* Line-wing cutoff (Sec. 2.5).  A grid point i belongs to a line's window
+ * when |nu_i - nu0'| <= C, realised as the integer bounds
+ *   i_lo = max(0, ceil((nu0' - C - nu_min)/dnu)),
+ *   i_hi = min(n-1, floor((nu0' + C - nu_min)/dnu)).
+ *   HELK_CUT_ABS:     C = value                     [cm^-1]
+ *   HELK_CUT_LORENTZ: C = min(value * Gamma_L, cap)  (e.g. 500 Gamma_L, 100)
+ *   HELK_CUT_NONE:    every grid point (the full Voigt profile)
+ * The truncated profile is not renormalised. */
+enum { HELK_CUT_ABS = 0, HELK_CUT_LORENTZ = 1, HELK_CUT_NONE = 2 };
+typedef struct {
+    int32_t kind;
+    double value;
+    double cap;
+} helk_cutoff;
+
+/* Line list as structure-of-arrays of n doubles each (Sec. 2.3).
+ *   nu0        line-centre wavenumber [cm^-1]                 (required)
+ *   S0         integrated strength [cm/molecule] at T0 = 296 K if E_lower
+ *              is given, else at the requested T               (required)
+ *   E_lower    lower-state energy [cm^-1]; NULL: no T scaling of S
+ *   gamma_air  air-broadening coefficient [cm^-1/atm]          (required)
+ *   gamma_self self-broadening coefficient; NULL: = gamma_air
+ *   n_coll     temperature exponent; NULL: 0.5
+ *   delta      pressure shift [cm^-1/atm]; NULL: 0
+ * All values must be finite, S0 >= 0, gamma_* >= 0. */
+typedef struct {
+    const double *nu0, *S0, *E_lower, *gamma_air, *gamma_self, *n_coll, *delta;
+} helk_lines;
+
+/* Arithmetic of the Voigt stage.
+ *   HELK_PREC_F64:       FP64 throughout (reference form).
+ *   HELK_PREC_F32_KAHAN: FP32 profile evaluation and Kahan-compensated FP32
+ *                        accumulation, output converted to FP64.  Error vs the
+ *                        FP64 form <= 1e-5 relative where kappa exceeds 1e-8
+ *                        of its k-bin maximum. */
+enum { HELK_PREC_F64 = 0, HELK_PREC_F32_KAHAN = 1 };
+
+typedef struct {
+    int32_t precision;  /* HELK_PREC_*                                      */
+    int32_t accumulate; /* 0: kappa = weight*sigma, 1: kappa += weight*sigma */
+    double weight;      /* abundance weight X of Sec. 2.1 (mix before k-dist) */
+    double q_ratio;     /* Q(T0)/Q(T), used only when E_lower was uploaded   */
+    int32_t count_regions; /* 1: also count evaluations per method (slower;
+                              read with helk_opacity_stats)                   */
+} helk_opts;
+
+/* Create a context on CUDA device `device`, enqueueing on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; release it with helk_destroy. */
+helk_status helk_create(helk_ctx **out, int device, void *stream);
+
+/* Free the context and every device buffer it owns (synchronises first). */
+void helk_destroy(helk_ctx *ctx);
+
+/* Last error message of this context ("" if none).  Valid until the next
+ * call on the context. */
+const char *helk_last_error(const helk_ctx *ctx);
+
+/* Change the stream later work is enqueued on. */
+helk_status helk_set_stream(helk_ctx *ctx, void *stream);
+
+/* Wait for all work of the context and report kernel-side errors. */
+helk_status helk_sync(helk_ctx *ctx);
+
+/* Upload (copy) a line list into context-owned device memory and order it
+ * by nu0 (stable), replacing any previous list.  `on_device` = 0: the
+ * pointers in *lines are host memory; 1: device memory.  n >= 0.
+ * Validation of values runs on the device and is reported here (the call
+ * synchronises the stream). */
+helk_status helk_lines_upload(helk_ctx *ctx, const helk_lines *lines,
+                              int64_t n, int32_t on_device);
+
+/* Opacity of the uploaded lines at one condition (Sec. 2.3-2.5):
+ *   kappa_out[i] (=|+=) weight * sum_lines S' H_V(a, u_i),
+ *   S' = S sqrt(ln2/pi)/Gamma_D, u_i = sqrt(ln2)(nu_i - nu0')/Gamma_D.
+ * kappa_out: device pointer to grid->n doubles, or NULL to use a buffer
+ * owned by the context (read by helk_kdist with kappa == NULL).
+ * T > 0, P >= 0, mass > 0.  opts may be NULL (FP64, weight 1, q_ratio 1). */
+helk_status helk_opacity(helk_ctx *ctx, double T, double P_atm,
+                         double mass_amu, const helk_cutoff *cut,
+                         const helk_grid *grid, const helk_opts *opts,
+                         double *kappa_out);
+
+/* Statistics of the last helk_opacity: number of (line, grid point) Voigt
+ * evaluations and, if region_counts != NULL (4 entries; the last opacity
+ * must have run with count_regions), how many fell in each method
+ * [Algorithm 916, GH3, GH1] plus the number of Algorithm 916 series terms
+ * summed.  Synchronises. */
+helk_status helk_opacity_stats(helk_ctx *ctx, int64_t *n_evals,
+                               int64_t *region_counts);
+
+/* k-distribution tables (Sec. 2.2, 2.6) of an opacity array of n points cut
+ * into nbins equal contiguous bins (n % nbins == 0, N_b = n/nbins):
+ *   - each bin sorted ascending: k_j, j = 0..N_b-1, on g_j = (j + 1/2)/N_b;
+ *   - ncheb coefficients c_k of the least-squares fit
+ *       ln max(k(g), kappa_floor) ~ sum_k c_k T_k(2g - 1);
+ *   - the bin mean of kappa (= int_0^1 k(g) dg, Sec. 2.1).
+ * kappa: device pointer (NULL = the context's buffer from helk_opacity).
+ * coeffs: nbins*ncheb doubles, row-major [bin][k]; mean: nbins doubles or
+ * NULL; both host memory if out_on_host != 0 (the call then synchronises)
+ * else device memory.  kg_out: optional device pointer to n doubles that
+ * receives the sorted values.  1 <= ncheb <= 32, ncheb <= N_b.
+ * The sorted values equal those of any correct ascending sort, bit for
+ * bit. */
+helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
+                       int32_t nbins, int32_t ncheb, double kappa_floor,
+                       double *coeffs, double *mean, int32_t out_on_host,
+                       double *kg_out);
+
+/* Stage timing (tracing).  With profiling on, the library records a CUDA
+ * event pair on the context stream around each stage it launches:
+ *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.5)
+ *   HELK_STAGE_VOIGT     the Voigt/opacity kernel (Sec. 2.4-2.5)
+ *   HELK_STAGE_KDIST     per-bin sort and Chebyshev fit (Sec. 2.6)
+ *   HELK_STAGE_SETUP     one-time pseudo-inverse of the Chebyshev basis
+ * helk_stage_times synchronises and writes, for each stage, the summed
+ * device time in ms (ms[HELK_NSTAGES]) and launch count (count, optional)
+ * since profiling was last switched on; at most 65536 pairs per stage are
+ * kept (later ones are dropped and flagged by count < 0). */
+enum { HELK_STAGE_LINEPREP = 0, HELK_STAGE_VOIGT = 1, HELK_STAGE_KDIST = 2,
+       HELK_STAGE_SETUP = 3, HELK_NSTAGES = 4 };
+helk_status helk_set_profiling(helk_ctx *ctx, int32_t on);
+helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELK_H */

@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
  * benchmark's CPU-baseline leg may load this library.  The product path (the
- * CUDA library under paper_1503_03806_gb300/csrc) shares no code, header,
+ * CUDA library of the paper_1503_03806_gb300 package) shares no code, header,
  * table or constant generator with this file.
  *
  * Built with `gcc -O2 -ffp-contract=off` so that every + - * / is a single

@@ -1,0 +1,408 @@
+// helk_api.cu -- the C ABI (include/helk.h): argument checks, context-owned
+// device buffers, and the order of kernel launches for each entry point.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstddef>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "helk_internal.cuh"
+
+using namespace helk;
+
+namespace helk {
+
+helk_status set_err(helk_ctx *c, helk_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+helk_status cuda_check(helk_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return HELK_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_err(c, HELK_ERR_OOM, std::string(what) + ": out of device memory");
+  }
+  return set_err(c, HELK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+helk_status ensure_buf(helk_ctx *c, void **p, int64_t *cap_bytes, int64_t bytes, const char *what) {
+  if (bytes <= *cap_bytes && *p) return HELK_OK;
+  if (*p) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, what);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap_bytes = 0;
+  }
+  int64_t alloc = bytes < 256 ? 256 : bytes;
+  cudaError_t e = cudaMalloc(p, (size_t)alloc);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_check(c, e, what);
+  }
+  *cap_bytes = alloc;
+  return HELK_OK;
+}
+
+constexpr int64_t EV_MAX_PAIRS = 65536;
+
+void stage_begin(helk_ctx *c, int stage) {
+  if (!c->profiling) return;
+  auto &v = c->ev[stage];
+  const int64_t i = c->ev_used[stage];
+  if (i >= EV_MAX_PAIRS) {
+    c->ev_overflow[stage] = true;
+    return;
+  }
+  while ((int64_t)v.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      c->ev_overflow[stage] = true;
+      return;
+    }
+    v.push_back(e);
+  }
+  cudaEventRecord(v[2 * i], c->stream);
+}
+
+void stage_end(helk_ctx *c, int stage) {
+  if (!c->profiling || c->ev_overflow[stage]) return;
+  const int64_t i = c->ev_used[stage];
+  if (i >= EV_MAX_PAIRS || (int64_t)c->ev[stage].size() < 2 * (i + 1)) return;
+  cudaEventRecord(c->ev[stage][2 * i + 1], c->stream);
+  c->ev_used[stage] = i + 1;
+}
+
+}  // namespace helk
+
+#define HELK_TRY(expr)              \
+  do {                              \
+    helk_status _s = (expr);        \
+    if (_s != HELK_OK) return _s;   \
+  } while (0)
+
+static helk_status bind_device(helk_ctx *c) {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != c->device) return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice");
+  return HELK_OK;
+}
+
+static bool is_fin(double v) { return std::isfinite(v); }
+
+extern "C" {
+
+helk_status helk_create(helk_ctx **out, int device, void *stream) {
+  if (!out) return HELK_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return HELK_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return HELK_ERR_INVALID_ARG;
+  helk_ctx *c = new (std::nothrow) helk_ctx();
+  if (!c) return HELK_ERR_OOM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return HELK_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (cudaMalloc(&c->stats, sizeof(DevStats)) != cudaSuccess ||
+      cudaMallocHost(&c->stats_host, sizeof(DevStats)) != cudaSuccess) {
+    cudaGetLastError();
+    helk_destroy(c);
+    return HELK_ERR_OOM;
+  }
+  memset(c->stats_host, 0, sizeof(DevStats));
+  if (cudaMemset(c->stats, 0, sizeof(DevStats)) != cudaSuccess) {
+    helk_destroy(c);
+    return HELK_ERR_CUDA;
+  }
+  *out = c;
+  return HELK_OK;
+}
+
+void helk_destroy(helk_ctx *c) {
+  if (!c) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
+                  c->delta, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
+                  c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
+                  c->mean_dev, c->tmp};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  if (c->stats_host) cudaFreeHost(c->stats_host);
+  for (int st = 0; st < HELK_NSTAGES; ++st)
+    for (cudaEvent_t e : c->ev[st]) cudaEventDestroy(e);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete c;
+}
+
+const char *helk_last_error(const helk_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+helk_status helk_set_stream(helk_ctx *c, void *stream) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return HELK_OK;
+}
+
+helk_status helk_sync(helk_ctx *c) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  HELK_TRY(bind_device(c));
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "stream synchronize"));
+  HELK_TRY(cuda_check(c, cudaMemcpy(c->stats_host, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost),
+                      "read status"));
+  if (c->stats_host->err_flags & ERRF_TIMEOUT)
+    return set_err(c, HELK_ERR_TIMEOUT, "a kernel's bounded wait on a bulk copy gave up");
+  return HELK_OK;
+}
+
+helk_status helk_lines_upload(helk_ctx *c, const helk_lines *L, int64_t n, int32_t on_device) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!L || n < 0 || n > INT32_MAX - 1)
+    return set_err(c, HELK_ERR_INVALID_ARG, "lines_upload: null lines or n out of range");
+  if (n > 0 && (!L->nu0 || !L->S0 || !L->gamma_air))
+    return set_err(c, HELK_ERR_INVALID_ARG, "lines_upload: nu0, S0 and gamma_air are required");
+  HELK_TRY(bind_device(c));
+  const int64_t bytes = (n > 0 ? n : 1) * 8;
+  double **dst[7] = {&c->nu0, &c->S0, &c->El, &c->gair, &c->gself, &c->ncoll, &c->delta};
+  const double *src[7] = {L->nu0, L->S0, L->E_lower, L->gamma_air, L->gamma_self, L->n_coll, L->delta};
+  if (bytes > c->lines_cap) {
+    HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "lines_upload"));
+    for (auto d : dst)
+      if (*d) {
+        cudaFree(*d);
+        *d = nullptr;
+      }
+    c->lines_cap = 0;
+    for (auto d : dst) HELK_TRY(cuda_check(c, cudaMalloc((void **)d, (size_t)bytes), "lines_upload alloc"));
+    c->lines_cap = bytes;
+  }
+  c->nlines = 0;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int f = 0; f < 7; ++f)
+    if (src[f] && n > 0)
+      HELK_TRY(cuda_check(c, cudaMemcpyAsync(*dst[f], src[f], (size_t)(n * 8), kind, c->stream),
+                          "lines_upload copy"));
+  c->has_E = L->E_lower != nullptr;
+  c->has_gself = L->gamma_self != nullptr;
+  c->has_ncoll = L->n_coll != nullptr;
+  c->has_delta = L->delta != nullptr;
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, sizeof(DevStats), c->stream), "lines_upload"));
+  HELK_TRY(cuda_check(c, launch_validate_lines(c, n), "validate lines"));
+  HELK_TRY(cuda_check(c, cudaMemcpyAsync(c->stats_host, c->stats, sizeof(DevStats),
+                                         cudaMemcpyDeviceToHost, c->stream),
+                      "lines_upload"));
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "lines_upload"));
+  if (c->stats_host->bad_lines)
+    return set_err(c, HELK_ERR_INVALID_ARG,
+                   "lines_upload: " + std::to_string(c->stats_host->bad_lines) +
+                       " lines with non-finite or negative values");
+  if (c->stats_host->unsorted) {
+    HELK_TRY(cuda_check(c, launch_sort_lines(c, n), "sort lines"));
+    HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sort lines"));
+  }
+  c->nlines = n;
+  c->have_opacity = false;
+  return HELK_OK;
+}
+
+static helk_status check_condition(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
+                                   const helk_grid *g, const helk_opts &o) {
+  if (!cut || !g) return set_err(c, HELK_ERR_INVALID_ARG, "null cutoff or grid");
+  if (!(is_fin(T) && T > 0.0)) return set_err(c, HELK_ERR_INVALID_ARG, "T must be finite and > 0");
+  if (!(is_fin(P) && P >= 0.0)) return set_err(c, HELK_ERR_INVALID_ARG, "P must be finite and >= 0");
+  if (!(is_fin(mass) && mass > 0.0)) return set_err(c, HELK_ERR_INVALID_ARG, "mass must be > 0");
+  if (!(is_fin(g->nu_min) && is_fin(g->dnu) && g->dnu > 0.0))
+    return set_err(c, HELK_ERR_INVALID_ARG, "grid: nu_min finite, dnu > 0 required");
+  if (g->n <= 0 || g->n > INT32_MAX - 4096)
+    return set_err(c, HELK_ERR_INVALID_ARG, "grid: n must be in [1, 2^31 - 4097]");
+  if (cut->kind < HELK_CUT_ABS || cut->kind > HELK_CUT_NONE)
+    return set_err(c, HELK_ERR_INVALID_ARG, "cutoff: unknown kind");
+  if (cut->kind != HELK_CUT_NONE && !(is_fin(cut->value) && cut->value >= 0.0))
+    return set_err(c, HELK_ERR_INVALID_ARG, "cutoff: value must be finite and >= 0");
+  if (cut->kind == HELK_CUT_LORENTZ && !(is_fin(cut->cap) && cut->cap >= 0.0))
+    return set_err(c, HELK_ERR_INVALID_ARG, "cutoff: cap must be finite and >= 0");
+  if (o.precision != HELK_PREC_F64 && o.precision != HELK_PREC_F32_KAHAN)
+    return set_err(c, HELK_ERR_INVALID_ARG, "opts: unknown precision");
+  if (!is_fin(o.weight) || !(is_fin(o.q_ratio) && o.q_ratio > 0.0))
+    return set_err(c, HELK_ERR_INVALID_ARG, "opts: weight finite and q_ratio > 0 required");
+  return HELK_OK;
+}
+
+static helk_opts default_opts() {
+  helk_opts o;
+  o.precision = HELK_PREC_F64;
+  o.accumulate = 0;
+  o.weight = 1.0;
+  o.q_ratio = 1.0;
+  o.count_regions = 0;
+  return o;
+}
+
+helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
+                         const helk_grid *g, const helk_opts *opts, double *kappa_out) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  const helk_opts o = opts ? *opts : default_opts();
+  HELK_TRY(check_condition(c, T, P, mass, cut, g, o));
+  if (o.precision != HELK_PREC_F64)
+    return set_err(c, HELK_ERR_UNSUPPORTED, "opacity: precision not built");
+  if (!c->nu0) return set_err(c, HELK_ERR_STATE, "opacity: no line list uploaded");
+  HELK_TRY(bind_device(c));
+  double *kappa = kappa_out;
+  if (!kappa) {
+    HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
+    kappa = c->kappa;
+  }
+  const int64_t nl = c->nlines > 0 ? c->nlines : 1;
+  HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
+  HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, nl * 8, "line keys"));
+  const int tile = voigt_tile_points(o.precision);
+  const int64_t ntiles = (g->n + tile - 1) / tile;
+  if (ntiles > c->tile_cap) {
+    if (c->tile_lo) cudaFree(c->tile_lo);
+    if (c->tile_hi) cudaFree(c->tile_hi);
+    c->tile_lo = c->tile_hi = nullptr;
+    c->tile_cap = 0;
+    HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_lo, (size_t)ntiles * 4), "tile map"));
+    HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_hi, (size_t)ntiles * 4), "tile map"));
+    c->tile_cap = ntiles;
+  }
+  // reset per-call statistics (keep error flags)
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, offsetof(DevStats, err_flags), c->stream), "stats"));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->wmax, 0xFF, sizeof(long long), c->stream), "stats"));
+  if (c->nlines > 0) {
+    stage_begin(c, HELK_STAGE_LINEPREP);
+    HELK_TRY(cuda_check(c, launch_lineprep(c, T, P, mass, o.q_ratio, *cut, *g, o.precision), "lineprep"));
+    HELK_TRY(cuda_check(c, launch_tilemap(c, *g, tile, ntiles), "tilemap"));
+    stage_end(c, HELK_STAGE_LINEPREP);
+    stage_begin(c, HELK_STAGE_VOIGT);
+    HELK_TRY(cuda_check(c, launch_voigt(c, *g, o, kappa, ntiles), "voigt"));
+    stage_end(c, HELK_STAGE_VOIGT);
+  } else if (!o.accumulate) {
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
+  }
+  c->last_n = g->n;
+  c->have_opacity = (kappa == c->kappa);
+  c->last_counted_regions = o.count_regions != 0;
+  return HELK_OK;
+}
+
+helk_status helk_opacity_stats(helk_ctx *c, int64_t *n_evals, int64_t *region_counts) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  HELK_TRY(helk_sync(c));
+  if (n_evals) *n_evals = (int64_t)c->stats_host->evals;
+  if (region_counts) {
+    if (!c->last_counted_regions)
+      return set_err(c, HELK_ERR_STATE, "opacity_stats: last opacity ran without count_regions");
+    for (int r = 0; r < 4; ++r) region_counts[r] = (int64_t)c->stats_host->region[r];
+  }
+  return HELK_OK;
+}
+
+helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbins, int32_t ncheb,
+                       double kappa_floor, double *coeffs, double *mean, int32_t out_on_host,
+                       double *kg_out) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n <= 0 || n > INT32_MAX || nbins <= 0 || n % nbins)
+    return set_err(c, HELK_ERR_INVALID_ARG, "kdist: n must be a positive multiple of nbins");
+  const int64_t nb = n / nbins;
+  if (ncheb < 1 || ncheb > 32 || ncheb > nb)
+    return set_err(c, HELK_ERR_INVALID_ARG, "kdist: need 1 <= ncheb <= min(32, n/nbins)");
+  if (!(is_fin(kappa_floor) && kappa_floor > 0.0))
+    return set_err(c, HELK_ERR_INVALID_ARG, "kdist: kappa_floor must be finite and > 0");
+  if (!coeffs) return set_err(c, HELK_ERR_INVALID_ARG, "kdist: coeffs is required");
+  if (!kappa) {
+    if (!c->have_opacity || c->last_n != n)
+      return set_err(c, HELK_ERR_STATE, "kdist: no context opacity of this size");
+    kappa = c->kappa;
+  }
+  HELK_TRY(bind_device(c));
+  if (c->pinv_nb != nb || c->pinv_ncheb != ncheb || !c->pinv) {
+    HELK_TRY(ensure_buf(c, (void **)&c->pinv, &c->pinv_cap, nb * ncheb * 8, "kdist pseudo-inverse"));
+    HELK_TRY(ensure_buf(c, &c->tmp, &c->tmp_cap, nb * ncheb * 8, "kdist pseudo-inverse"));
+    stage_begin(c, HELK_STAGE_SETUP);
+    HELK_TRY(cuda_check(c, launch_pinv(c, nb, ncheb, (double *)c->tmp), "kdist pseudo-inverse"));
+    stage_end(c, HELK_STAGE_SETUP);
+    c->pinv_nb = nb;
+    c->pinv_ncheb = ncheb;
+  }
+  if (nb > kdist_smem_max_points(c)) {
+    if (n * 8 > c->sort_cap) {
+      HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "kdist"));
+      if (c->sort_a) cudaFree(c->sort_a);
+      if (c->sort_b) cudaFree(c->sort_b);
+      c->sort_a = c->sort_b = nullptr;
+      c->sort_cap = 0;
+      HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->sort_a, (size_t)n * 8), "kdist scratch"));
+      HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->sort_b, (size_t)n * 8), "kdist scratch"));
+      c->sort_cap = n * 8;
+    }
+  }
+  double *cdst = coeffs, *mdst = mean;
+  if (out_on_host) {
+    HELK_TRY(ensure_buf(c, (void **)&c->coef_dev, &c->coef_cap, (int64_t)nbins * ncheb * 8, "kdist out"));
+    HELK_TRY(ensure_buf(c, (void **)&c->mean_dev, &c->mean_cap, (int64_t)nbins * 8, "kdist out"));
+    cdst = c->coef_dev;
+    mdst = c->mean_dev;
+  }
+  stage_begin(c, HELK_STAGE_KDIST);
+  HELK_TRY(cuda_check(c, launch_kdist_bins(c, kappa, n, nbins, ncheb, kappa_floor, cdst, mdst, kg_out),
+                      "kdist"));
+  stage_end(c, HELK_STAGE_KDIST);
+  if (out_on_host) {
+    HELK_TRY(cuda_check(c, cudaMemcpyAsync(coeffs, cdst, (size_t)nbins * ncheb * 8, cudaMemcpyDeviceToHost,
+                                           c->stream),
+                        "kdist copy"));
+    if (mean)
+      HELK_TRY(cuda_check(c, cudaMemcpyAsync(mean, mdst, (size_t)nbins * 8, cudaMemcpyDeviceToHost, c->stream),
+                          "kdist copy"));
+    HELK_TRY(helk_sync(c));
+  }
+  return HELK_OK;
+}
+
+helk_status helk_set_profiling(helk_ctx *c, int32_t on) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->profiling = on != 0;
+  for (int st = 0; st < HELK_NSTAGES; ++st) {
+    c->ev_used[st] = 0;
+    c->ev_overflow[st] = false;
+  }
+  return HELK_OK;
+}
+
+helk_status helk_stage_times(helk_ctx *c, double *ms, int64_t *count) {
+  if (!c || !ms) return HELK_ERR_INVALID_ARG;
+  HELK_TRY(bind_device(c));
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "stage_times"));
+  for (int st = 0; st < HELK_NSTAGES; ++st) {
+    double tot = 0.0;
+    for (int64_t i = 0; i < c->ev_used[st]; ++i) {
+      float t = 0.f;
+      HELK_TRY(cuda_check(c, cudaEventElapsedTime(&t, c->ev[st][2 * i], c->ev[st][2 * i + 1]),
+                          "stage_times"));
+      tot += t;
+    }
+    ms[st] = tot;
+    if (count) count[st] = c->ev_overflow[st] ? -c->ev_used[st] : c->ev_used[st];
+  }
+  return HELK_OK;
+}
+
+}  // extern "C"

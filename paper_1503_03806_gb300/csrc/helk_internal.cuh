@@ -1,0 +1,208 @@
+// helk_internal.cuh -- shared declarations of the sm_103a HELIOS-K library.
+//
+// Device data layout (HBM):
+//   line list  SoA doubles, ordered by nu0 (stable), one array per field.
+//   LineRec64  64-byte per-line record of one (T, P) condition (FP64 form).
+//   LineRec32  48-byte per-line record (FP32 form), strengths scaled by 2^-E.
+//   ckey       per-line floor((nu0 - nu_min)/dnu) as double; non-decreasing
+//              in list order, used to map grid tiles to line ranges.
+//   kappa      doubles on the uniform grid.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/helk.h"
+
+namespace helk {
+
+// ------------------------------------------------------------ constants --
+// CGS; CODATA 2018 exact SI values.  T0 = 296 K (Sec. 2.3).
+constexpr double KB = 1.380649e-16;       // erg / K
+constexpr double CLIGHT = 2.99792458e10;  // cm / s
+constexpr double AMU = 1.66053906660e-24; // g
+constexpr double C2 = 1.4387768775039338021;  // h c / k_B [cm K]
+constexpr double T0 = 296.0;
+constexpr double PI = 3.1415926535897932384626;
+constexpr double LN2 = 0.69314718055994530941723;
+constexpr double SQRTLN2 = 0.83255461115769775635316;    // sqrt(ln 2)
+constexpr double SQRTLN2PI = 0.46971863934982566688617;  // sqrt(ln 2 / pi)
+constexpr double SQRTPI = 1.7724538509055160272982;
+constexpr double INV_SQRTPI = 0.56418958354775628694808;
+constexpr double GH3_T = 1.2247448713915890490986;       // sqrt(3/2)
+// Region thresholds on r^2 = a^2 + u^2 (Sec. 2.5)
+constexpr double R2_GH3 = 100.0;
+constexpr double R2_GH1 = 1.0e6;
+// Algorithm 916 series step and tail width: terms with |n h -+ x| > A916_TAIL
+// are below e^{-38} of the largest one and are skipped.
+constexpr double A916_H = 0.5;
+constexpr double A916_TAIL = 6.2;
+constexpr int A916_S1_TERMS = 13;  // e^{-(nh)^2} < 1e-18 beyond n = 13
+
+// ------------------------------------------------------------ records ---
+struct __align__(16) LineRec64 {
+  double nu0p;     // shifted centre nu0 + delta P
+  double ku;       // sqrt(ln2) / Gamma_D
+  double a;        // damping sqrt(ln2) Gamma_L / Gamma_D
+  double a2;       // a*a (rounded once, as the oracle does)
+  double Sp;       // S sqrt(ln2/pi) / Gamma_D
+  double erfcx_a;  // erfcx(a) (core region only; 0 if a >= 10)
+  double sig1;     // sum_n e^{-(nh)^2}/((nh)^2 + a^2) (core region only)
+  int32_t ilo, ihi;  // window, empty when ilo > ihi
+};
+static_assert(sizeof(LineRec64) == 64, "LineRec64 must be 64 bytes");
+
+struct __align__(16) LineRec32 {
+  int32_t c;       // reference grid index near the shifted centre
+  int32_t ilo, ihi;
+  float phi_k;     // (nu0' - nu_c) * ku: u_i = (i - c) beta - phi_k
+  float beta;      // dnu * ku
+  float a;         // damping
+  float a2;        // a*a
+  float P1;        // Sp a / sqrt(pi)      (scaled)   GH1 numerator
+  float P3;        // Sp a (sqrt(pi)/6)/pi (scaled)   GH3 numerator
+  float Sp;        // Sp                   (scaled)   core region
+  float erfcx_a;   // erfcx(a)
+  float sig1;      // core series S1(a)
+};
+static_assert(sizeof(LineRec32) == 48, "LineRec32 must be 48 bytes");
+
+// Device-side statistics and error flags of the last call.
+struct DevStats {
+  unsigned long long evals;         // sum of window sizes
+  unsigned long long region[4];     // evaluations per method (optional):
+                                    // [916, GH3, GH1, 916 series terms]
+  long long wmax;                   // max half-width of a window in points
+  unsigned long long spmax_bits;    // max S' (non-negative double bits)
+  int err_flags;                    // ERRF_*
+  int bad_lines;                    // validation failures at upload
+  int unsorted;                     // upload: nu0 not ordered
+  int pad;
+};
+enum { ERRF_TIMEOUT = 1 };
+
+// ---------------------------------------------------------- the context --
+}  // namespace helk
+
+struct helk_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  // line list (sorted SoA)
+  int64_t nlines = 0;
+  bool has_E = false, has_gself = false, has_ncoll = false, has_delta = false;
+  double *nu0 = nullptr, *S0 = nullptr, *El = nullptr, *gair = nullptr,
+         *gself = nullptr, *ncoll = nullptr, *delta = nullptr;
+  int64_t lines_cap = 0;
+  // per-call scratch
+  helk::LineRec64 *rec64 = nullptr;
+  helk::LineRec32 *rec32 = nullptr;
+  double *ckey = nullptr;
+  int64_t ckey_cap = 0;
+  int64_t rec_cap = 0;
+  int32_t *tile_lo = nullptr, *tile_hi = nullptr;
+  int64_t tile_cap = 0;
+  helk::DevStats *stats = nullptr;      // device
+  helk::DevStats *stats_host = nullptr; // pinned
+  // opacity output owned by the context
+  double *kappa = nullptr;
+  int64_t kappa_cap = 0;
+  int64_t last_n = 0;
+  bool have_opacity = false;
+  bool last_counted_regions = false;
+  // k-distribution scratch
+  unsigned long long *sort_a = nullptr, *sort_b = nullptr;
+  int64_t sort_cap = 0;
+  double *pinv = nullptr;  // pseudo-inverse of the Chebyshev design matrix
+  int64_t pinv_cap = 0, pinv_nb = 0;
+  int pinv_ncheb = 0;
+  double *coef_dev = nullptr, *mean_dev = nullptr;
+  int64_t coef_cap = 0, mean_cap = 0;
+  // generic upload scratch
+  void *tmp = nullptr;
+  int64_t tmp_cap = 0;
+  // stage timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev[HELK_NSTAGES];  // start/end pairs
+  int64_t ev_used[HELK_NSTAGES] = {0, 0, 0, 0};
+  bool ev_overflow[HELK_NSTAGES] = {false, false, false, false};
+};
+
+namespace helk {
+
+// ------------------------------------------------------------- helpers --
+// Stage timing: record the start / end event of one stage launch.
+void stage_begin(helk_ctx *c, int stage);
+void stage_end(helk_ctx *c, int stage);
+helk_status set_err(helk_ctx *c, helk_status st, const std::string &msg);
+helk_status cuda_check(helk_ctx *c, cudaError_t e, const char *what);
+// Grow a device buffer to at least `bytes` (contents are not kept).
+helk_status ensure_buf(helk_ctx *c, void **p, int64_t *cap_bytes, int64_t bytes,
+                       const char *what);
+
+// Bounded wait on an mbarrier phase: returns false (and sets ERRF_TIMEOUT in
+// *flags) if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_smem, uint32_t parity,
+                                                  int *flags, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar_smem), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  atomicOr(flags, ERRF_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// 1-D bulk TMA copy global -> shared, completing on an mbarrier.  dst, src
+// 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(uint32_t dst_smem, const void *src, uint32_t bytes,
+                                            uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_smem),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// ---------------------------------------------------------- launchers ---
+// k_lines.cu
+cudaError_t launch_validate_lines(helk_ctx *c, int64_t n);
+cudaError_t launch_sort_lines(helk_ctx *c, int64_t n);  // orders SoA by nu0
+cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double q_ratio,
+                            const helk_cutoff &cut, const helk_grid &g, int precision);
+cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t ntiles);
+// k_voigt.cu
+int voigt_tile_points(int precision);
+cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, double *kappa,
+                         int64_t ntiles);
+// k_kdist.cu
+cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
+cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
+                              double kappa_floor, double *coef, double *mean, double *kg_out);
+int64_t kdist_smem_max_points(helk_ctx *c);
+
+}  // namespace helk

@@ -1,0 +1,316 @@
+// k_kdist.cu -- k-distribution tables (Sec. 2.2, 2.6).
+//
+// One CTA per bin: the bin's opacities (non-negative doubles, ordered as
+// their IEEE bit patterns) are radix-sorted in shared memory when they fit
+// (else in a global ping-pong buffer), then the same CTA computes
+// L_j = ln max(k_j, kappa_floor) on g_j = (j + 1/2)/N_b and the least-squares
+// Chebyshev coefficients c = P L, where P is the pseudo-inverse of the design
+// matrix (shared by all bins of one size; computed once by k_pinv).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "helk_internal.cuh"
+
+namespace helk {
+
+constexpr int KD_THREADS = 512;
+constexpr int KD_WARPS = KD_THREADS / 32;
+constexpr int NCHEB_MAX = 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt_kd() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------ pseudo-inverse --
+// The design matrix A_jk = T_k(t_j), t_j = (2j+1)/N_b - 1, is the same for
+// every bin, so its pseudo-inverse P = R^{-1} Q_1^T (Householder QR, A = QR)
+// is computed once per (N_b, n_cheb) and each bin's coefficients are
+// c = P L.  One CTA; A is built column-major in `work` (n_cheb columns of
+// N_b), Q_1 is formed in `P` and turned into P column by column.
+constexpr int PI_THREADS = 512;
+
+__device__ double block_sum_pi(double v, double *red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < PI_THREADS / 32; ++i) s += red[i];
+  return s;
+}
+
+__global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, double *work,
+                                                     double *vtv_out, double *P) {
+  __shared__ double red[PI_THREADS / 32];
+  __shared__ double R[NCHEB_MAX * NCHEB_MAX];
+  __shared__ double vtv[NCHEB_MAX];
+  const int tid = threadIdx.x;
+  // A, column-major
+  for (int64_t j = tid; j < nb; j += PI_THREADS) {
+    const double t = (double)(2 * j + 1) / (double)nb - 1.0;
+    double tkm1 = 1.0, tk = t;
+    work[j] = 1.0;
+    if (ncheb > 1) work[nb + j] = t;
+    for (int k = 2; k < ncheb; ++k) {
+      const double tn = 2.0 * t * tk - tkm1;
+      tkm1 = tk;
+      tk = tn;
+      work[(int64_t)k * nb + j] = tn;
+    }
+  }
+  __syncthreads();
+  // Householder QR: column c becomes the reflector v_c (rows c..nb-1)
+  for (int c = 0; c < ncheb; ++c) {
+    double *col = work + (int64_t)c * nb;
+    double s = 0.0;
+    for (int64_t j = c + tid; j < nb; j += PI_THREADS) s += col[j] * col[j];
+    const double norm = sqrt(block_sum_pi(s, red));
+    const double x0 = col[c];
+    const double alpha = x0 > 0.0 ? -norm : norm;
+    __syncthreads();
+    if (tid == 0) col[c] = x0 - alpha;
+    __syncthreads();
+    s = 0.0;
+    for (int64_t j = c + tid; j < nb; j += PI_THREADS) s += col[j] * col[j];
+    const double vv = block_sum_pi(s, red);
+    if (tid == 0) {
+      vtv[c] = vv;
+      R[c * NCHEB_MAX + c] = alpha;
+    }
+    for (int cc = c + 1; cc < ncheb; ++cc) {
+      double *oc = work + (int64_t)cc * nb;
+      s = 0.0;
+      for (int64_t j = c + tid; j < nb; j += PI_THREADS) s += col[j] * oc[j];
+      const double f = 2.0 * block_sum_pi(s, red) / vv;
+      for (int64_t j = c + tid; j < nb; j += PI_THREADS) oc[j] -= f * col[j];
+      __syncthreads();
+      if (tid == 0) R[c * NCHEB_MAX + cc] = oc[c];
+    }
+    __syncthreads();
+  }
+  // Q_1 = H_0 H_1 ... H_{n-1} [I; 0], column-major in P
+  for (int k = 0; k < ncheb; ++k)
+    for (int64_t j = tid; j < nb; j += PI_THREADS) P[(int64_t)k * nb + j] = (j == k) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int c = ncheb - 1; c >= 0; --c) {
+    const double *v = work + (int64_t)c * nb;
+    for (int k = 0; k < ncheb; ++k) {
+      double *e = P + (int64_t)k * nb;
+      double s = 0.0;
+      for (int64_t j = c + tid; j < nb; j += PI_THREADS) s += v[j] * e[j];
+      const double f = 2.0 * block_sum_pi(s, red) / vtv[c];
+      for (int64_t j = c + tid; j < nb; j += PI_THREADS) e[j] -= f * v[j];
+      __syncthreads();
+    }
+  }
+  // P[:, j] = R^{-1} Q_1[j, :]^T, stored k-major (P[k*nb + j])
+  for (int64_t j = tid; j < nb; j += PI_THREADS) {
+    double p[NCHEB_MAX];
+    for (int k = ncheb - 1; k >= 0; --k) {
+      double v = P[(int64_t)k * nb + j];
+      for (int m = k + 1; m < ncheb; ++m) v -= R[k * NCHEB_MAX + m] * p[m];
+      p[k] = v / R[k * NCHEB_MAX + k];
+    }
+    for (int k = 0; k < ncheb; ++k) P[(int64_t)k * nb + j] = p[k];
+  }
+  if (tid == 0 && vtv_out) vtv_out[0] = vtv[0];
+}
+
+cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
+  k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------- block-wide helpers --
+// Exclusive scan of KD_THREADS*8 counters h[0..4095] in place.
+__device__ void block_exscan_4096(uint32_t *h, uint32_t *wtot) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t loc[8];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    loc[i] = h[tid * 8 + i];
+    s += loc[i];
+  }
+  uint32_t v = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wtot[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < KD_WARPS ? wtot[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane < KD_WARPS) wtot[lane] = x;
+  }
+  __syncthreads();
+  uint32_t run = v - s + (w > 0 ? wtot[w - 1] : 0u);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[tid * 8 + i] = run;
+    run += loc[i];
+  }
+  __syncthreads();
+}
+
+// Stable LSD radix sort of nb 64-bit keys held in A (shared or global);
+// B is the second buffer.  Digits whose value is the same in every key are
+// skipped.  Returns the buffer holding the result.
+__device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned long long *B, int nb,
+                                              uint32_t *hist /*[256][KD_WARPS]*/, uint32_t *wtot,
+                                              unsigned long long diff) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (nb + KD_WARPS - 1) / KD_WARPS;
+  const int w0 = w * per, w1 = min(nb, w0 + per);
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = pass * 8;
+    if (((diff >> shift) & 0xFFull) == 0) continue;
+    for (int i = tid; i < 256 * KD_WARPS; i += KD_THREADS) hist[i] = 0;
+    __syncthreads();
+    for (int e0 = w0; e0 < w1; e0 += 32) {
+      const int e = e0 + lane;
+      const uint32_t d = e < w1 ? (uint32_t)((A[e] >> shift) & 0xFF) : 256u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (d < 256 && (peers & lanemask_lt_kd()) == 0) hist[d * KD_WARPS + w] += __popc(peers);
+    }
+    __syncthreads();
+    block_exscan_4096(hist, wtot);
+    for (int e0 = w0; e0 < w1; e0 += 32) {
+      const int e = e0 + lane;
+      const bool valid = e < w1;
+      const unsigned long long k = valid ? A[e] : 0ull;
+      const uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid) B[hist[d * KD_WARPS + w] + __popc(peers & lanemask_lt_kd())] = k;
+      __syncwarp();
+      if (valid && (peers & lanemask_lt_kd()) == 0) hist[d * KD_WARPS + w] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    unsigned long long *t = A;
+    A = B;
+    B = t;
+  }
+  return A;
+}
+
+// ---------------------------------------------------- per-bin sort + fit --
+template <bool SMEM_KEYS>
+__global__ void __launch_bounds__(KD_THREADS)
+    k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
+                const double *__restrict__ pinv, unsigned long long *gA, unsigned long long *gB,
+                double *__restrict__ coef, double *__restrict__ mean, double *__restrict__ kg_out) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint32_t hist[256 * KD_WARPS];
+  __shared__ uint32_t wtot[32];
+  __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
+  __shared__ double red[KD_WARPS][NCHEB_MAX + 1];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t off = (int64_t)blockIdx.x * nb;
+  unsigned long long *A, *B;
+  if (SMEM_KEYS) {
+    A = (unsigned long long *)dsm;
+    B = A + nb;
+  } else {
+    A = gA + off;
+    B = gB + off;
+  }
+  unsigned long long vand = ~0ull, vor = 0ull;
+  for (int j = tid; j < nb; j += KD_THREADS) {
+    const unsigned long long k = (unsigned long long)__double_as_longlong(kappa[off + j]);
+    A[j] = k;
+    vand &= k;
+    vor |= k;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vand &= __shfl_down_sync(0xffffffffu, vand, o);
+    vor |= __shfl_down_sync(0xffffffffu, vor, o);
+  }
+  if (lane == 0) {
+    red_and[w] = vand;
+    red_or[w] = vor;
+  }
+  __syncthreads();
+  vand = ~0ull;
+  vor = 0ull;
+  for (int i = 0; i < KD_WARPS; ++i) {
+    vand &= red_and[i];
+    vor |= red_or[i];
+  }
+  const unsigned long long *S = cta_radix_sort(A, B, nb, hist, wtot, vand ^ vor);
+  // sorted values out, c = P L and the bin sum
+  double b[NCHEB_MAX];
+#pragma unroll
+  for (int k = 0; k < NCHEB_MAX; ++k) b[k] = 0.0;
+  double ksum = 0.0;
+  for (int j = tid; j < nb; j += KD_THREADS) {
+    const double kv = __longlong_as_double((long long)S[j]);
+    if (kg_out) kg_out[off + j] = kv;
+    ksum += kv;
+    const double L = log(kv > kappa_floor ? kv : kappa_floor);
+#pragma unroll
+    for (int k = 0; k < NCHEB_MAX; ++k)
+      if (k < ncheb) b[k] += pinv[(int64_t)k * nb + j] * L;
+  }
+#pragma unroll
+  for (int k = 0; k < NCHEB_MAX; ++k) {
+    if (k < ncheb) {
+      const double v = warp_sum(b[k]);
+      if (lane == 0) red[w][k] = v;
+    }
+  }
+  {
+    const double v = warp_sum(ksum);
+    if (lane == 0) red[w][NCHEB_MAX] = v;
+  }
+  __syncthreads();
+  if (tid < ncheb) {
+    double s = 0.0;
+    for (int i = 0; i < KD_WARPS; ++i) s += red[i][tid];
+    coef[(int64_t)blockIdx.x * ncheb + tid] = s;
+  }
+  if (tid == NCHEB_MAX && mean) {
+    double s = 0.0;
+    for (int i = 0; i < KD_WARPS; ++i) s += red[i][NCHEB_MAX];
+    mean[blockIdx.x] = s / (double)nb;
+  }
+}
+
+int64_t kdist_smem_max_points(helk_ctx *c) {
+  // static smem of k_kdist_bin is ~25 KB; keep 1 KB slack
+  const int64_t fixed = 26 * 1024;
+  int64_t avail = (int64_t)c->max_smem_optin - fixed;
+  return avail > 0 ? avail / 16 : 0;
+}
+
+cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
+                              double kappa_floor, double *coef, double *mean, double *kg_out) {
+  const int nb = (int)(n / nbins);
+  if ((int64_t)nb <= kdist_smem_max_points(c)) {
+    const size_t smem = (size_t)nb * 16;
+    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_kdist_bin<true><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, c->pinv,
+                                                              nullptr, nullptr, coef, mean, kg_out);
+  } else {
+    k_kdist_bin<false><<<nbins, KD_THREADS, 0, c->stream>>>(
+        kappa, nb, ncheb, kappa_floor, c->pinv, c->sort_a, c->sort_b, coef, mean, kg_out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace helk

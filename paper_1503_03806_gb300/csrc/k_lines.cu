@@ -1,0 +1,395 @@
+// k_lines.cu -- line-list kernels: validation, ordering by nu0, per-condition
+// line preparation (Sec. 2.3-2.5) and the grid-tile -> line-range map.
+//
+// This translation unit is compiled with --fmad=false: the quantities that
+// decide which grid points a line covers (window bounds) and which method
+// evaluates a point (a, ku) must be the correctly rounded results of the
+// operations written here, with no contraction into FMA.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "helk_internal.cuh"
+
+namespace helk {
+
+// e^{-(n h)^2}, h = 1/2, n = 1..13: weights of the S1 series of
+// Algorithm 916 (depends on the line's damping only, so it is summed once
+// per line).
+__constant__ double c_exp_nh2[A916_S1_TERMS] = {
+    0.77880078307140486825,  0.3678794411714423216,   0.10539922456186433678,
+    0.018315638888734180294, 0.0019304541362277092422, 0.0001234098040866795495,
+    4.7851173921290090896e-6, 1.1253517471925911451e-7, 1.6052280551856116087e-9,
+    1.3887943864964020595e-11, 7.2877240958196924193e-14, 2.3195228302435693883e-16,
+    4.477732441718301199e-19};
+
+// -------------------------------------------------------- validation ---
+__global__ void k_validate(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
+                           const double *__restrict__ El, const double *__restrict__ gair,
+                           const double *__restrict__ gself, const double *__restrict__ ncoll,
+                           const double *__restrict__ delta, DevStats *st) {
+  int bad = 0, unsorted = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    double v = nu0[l];
+    bool ok = isfinite(v) && isfinite(S0[l]) && S0[l] >= 0.0 && isfinite(gair[l]) && gair[l] >= 0.0;
+    if (El) ok = ok && isfinite(El[l]);
+    if (gself) ok = ok && isfinite(gself[l]) && gself[l] >= 0.0;
+    if (ncoll) ok = ok && isfinite(ncoll[l]);
+    if (delta) ok = ok && isfinite(delta[l]);
+    bad += !ok;
+    if (l + 1 < n && nu0[l + 1] < v) unsorted = 1;
+  }
+  if (bad) atomicAdd(&st->bad_lines, bad);
+  if (unsorted) atomicOr(&st->unsorted, 1);
+}
+
+cudaError_t launch_validate_lines(helk_ctx *c, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > c->num_sms * 8) blocks = c->num_sms * 8;
+  k_validate<<<blocks, 256, 0, c->stream>>>(n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
+                                            c->has_gself ? c->gself : nullptr,
+                                            c->has_ncoll ? c->ncoll : nullptr,
+                                            c->has_delta ? c->delta : nullptr, c->stats);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- stable LSD radix sort (pairs) --
+// Keys: 64-bit, values: 32-bit.  One pass per 8-bit digit; each pass is
+// upsweep (per-tile digit counts) -> exclusive scan -> downsweep (stable
+// scatter: warps own consecutive sub-ranges, ranks inside a warp batch come
+// from __match_any_sync).
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_TILE = 4096;  // elements per block
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const unsigned long long *__restrict__ keys,
+                                                           int64_t n, int shift, uint32_t *counts,
+                                                           int nblk) {
+  __shared__ uint32_t h[256];
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) h[d] = 0;
+  __syncthreads();
+  int64_t b0 = (int64_t)blockIdx.x * RS_TILE;
+  int64_t b1 = b0 + RS_TILE < n ? b0 + RS_TILE : n;
+  for (int64_t e = b0 + threadIdx.x; e < b1; e += RS_THREADS)
+    atomicAdd(&h[(keys[e] >> shift) & 0xFF], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) counts[(int64_t)d * nblk + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of m counts in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *counts, int64_t m) {
+  __shared__ uint32_t part[1024];
+  __shared__ uint32_t wsum[32];
+  int64_t per = (m + 1023) / 1024;
+  int64_t s0 = threadIdx.x * per, s1 = s0 + per < m ? s0 + per : m;
+  uint32_t s = 0;
+  for (int64_t i = s0; i < s1; ++i) s += counts[i];
+  // block exclusive scan of s
+  uint32_t v = s;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  uint32_t excl = v - s + (w > 0 ? wsum[w - 1] : 0u);
+  part[threadIdx.x] = excl;
+  for (int64_t i = s0; i < s1; ++i) {
+    uint32_t t = counts[i];
+    counts[i] = excl;
+    excl += t;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
+    const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+    unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+    const uint32_t *__restrict__ counts, int nblk) {
+  __shared__ uint32_t h[256 * RS_WARPS];  // [digit][warp]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 256 * RS_WARPS; i += RS_THREADS) h[i] = 0;
+  __syncthreads();
+  int64_t b0 = (int64_t)blockIdx.x * RS_TILE;
+  int64_t b1 = b0 + RS_TILE < n ? b0 + RS_TILE : n;
+  const int per = RS_TILE / RS_WARPS;
+  int64_t w0 = b0 + (int64_t)w * per, w1 = w0 + per < b1 ? w0 + per : b1;
+  // per-warp digit counts
+  for (int64_t e0 = w0; e0 < w1; e0 += 32) {
+    int64_t e = e0 + lane;
+    uint32_t d = e < w1 ? (uint32_t)((kin[e] >> shift) & 0xFF) : 256u + lane;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256 && (peers & lanemask_lt()) == 0) h[d * RS_WARPS + w] += __popc(peers);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t run = counts[(int64_t)d * nblk + blockIdx.x];
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      uint32_t t = h[d * RS_WARPS + ww];
+      h[d * RS_WARPS + ww] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  for (int64_t e0 = w0; e0 < w1; e0 += 32) {
+    int64_t e = e0 + lane;
+    bool valid = e < w1;
+    unsigned long long k = valid ? kin[e] : 0ull;
+    uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u + lane;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (valid) {
+      uint32_t pos = h[d * RS_WARPS + w] + __popc(peers & lanemask_lt());
+      kout[pos] = k;
+      vout[pos] = vin[e];
+    }
+    __syncwarp();
+    if (valid && (peers & lanemask_lt()) == 0) h[d * RS_WARPS + w] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+__global__ void k_line_keys(int64_t n, const double *__restrict__ nu0, unsigned long long *keys,
+                            uint32_t *vals) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    double v = nu0[l];
+    if (v == 0.0) v = 0.0;  // -0 -> +0
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    keys[l] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    vals[l] = (uint32_t)l;
+  }
+}
+
+__global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ src,
+                         double *__restrict__ dst) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x)
+    dst[l] = src[perm[l]];
+}
+
+cudaError_t launch_sort_lines(helk_ctx *c, int64_t n) {
+  if (n <= 1) return cudaSuccess;
+  const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  // scratch: 2 key arrays, 2 value arrays, counts, one double array
+  int64_t need = 2 * n * 8 + 2 * n * 4 + (int64_t)256 * nblk * 4 + n * 8 + 64;
+  helk_status st = ensure_buf(c, &c->tmp, &c->tmp_cap, need, "line sort scratch");
+  if (st != HELK_OK) return cudaErrorMemoryAllocation;
+  char *p = (char *)c->tmp;
+  unsigned long long *ka = (unsigned long long *)p;  p += n * 8;
+  unsigned long long *kb = (unsigned long long *)p;  p += n * 8;
+  uint32_t *va = (uint32_t *)p;                      p += n * 4;
+  uint32_t *vb = (uint32_t *)p;                      p += n * 4;
+  uint32_t *counts = (uint32_t *)p;                  p += (int64_t)256 * nblk * 4;
+  p = (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  double *dtmp = (double *)p;
+  int gb = (int)((n + 255) / 256);
+  if (gb > c->num_sms * 16) gb = c->num_sms * 16;
+  k_line_keys<<<gb, 256, 0, c->stream>>>(n, c->nu0, ka, va);
+  for (int pass = 0; pass < 8; ++pass) {
+    int shift = pass * 8;
+    k_rs_upsweep<<<nblk, RS_THREADS, 0, c->stream>>>(ka, n, shift, counts, nblk);
+    k_rs_scan<<<1, 1024, 0, c->stream>>>(counts, (int64_t)256 * nblk);
+    k_rs_downsweep<<<nblk, RS_THREADS, 0, c->stream>>>(ka, va, kb, vb, n, shift, counts, nblk);
+    unsigned long long *tk = ka; ka = kb; kb = tk;
+    uint32_t *tv = va; va = vb; vb = tv;
+  }
+  double *fields[7] = {c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
+                       c->has_gself ? c->gself : nullptr, c->has_ncoll ? c->ncoll : nullptr,
+                       c->has_delta ? c->delta : nullptr};
+  for (int f = 0; f < 7; ++f) {
+    if (!fields[f]) continue;
+    k_gather<<<gb, 256, 0, c->stream>>>(n, va, fields[f], dtmp);
+    cudaError_t e = cudaMemcpyAsync(fields[f], dtmp, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- line preparation --
+struct PrepArgs {
+  double T, P, mass, q_ratio;
+  int cut_kind;
+  double cut_value, cut_cap;
+  double nu_min, dnu;
+  int64_t ngrid;
+};
+
+// Per line and condition, in the operation order of the definitions:
+//   nu0' = nu0 + delta P                                   (Sec. 2.3 shift)
+//   S    = S0 (Q0/Q) e^{-c2E/T + c2E/T0} (1-e^{-c2 nu0/T})/(1-e^{-c2 nu0/T0})
+//   Gamma_L = (T0/T)^n (g_air (P - P/2) + g_self P/2)      (Sec. 2.3)
+//   Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c               (Sec. 2.4)
+//   a = sqrt(ln2) Gamma_L / Gamma_D, ku = sqrt(ln2)/Gamma_D,
+//   S' = S sqrt(ln2/pi) / Gamma_D, window from the cutoff   (Sec. 2.5)
+__global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
+                           const double *__restrict__ El, const double *__restrict__ gair,
+                           const double *__restrict__ gself, const double *__restrict__ ncoll,
+                           const double *__restrict__ delta, PrepArgs A, LineRec64 *__restrict__ rec,
+                           double *__restrict__ ckey, DevStats *st) {
+  unsigned long long evals = 0;
+  long long wmax = -1;
+  unsigned long long spmax = 0;
+  const double vth = sqrt(2.0 * LN2 * KB * A.T / (A.mass * AMU)) / CLIGHT;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const double v0 = nu0[l];
+    const double dl = delta ? delta[l] : 0.0;
+    const double ga = gair[l];
+    const double gs = gself ? gself[l] : ga;
+    const double nc = ncoll ? ncoll[l] : 0.5;
+    double S = S0[l];
+    const double nu0p = v0 + dl * A.P;
+    if (El) {
+      const double E = El[l];
+      const double boltz = exp(-C2 * E / A.T + C2 * E / T0);
+      const double stim = v0 > 0.0 ? expm1(-C2 * v0 / A.T) / expm1(-C2 * v0 / T0) : T0 / A.T;
+      S = S * A.q_ratio * boltz * stim;
+    }
+    const double tfac = (nc == 0.5) ? sqrt(T0 / A.T) : pow(T0 / A.T, nc);
+    const double pself = 0.5 * A.P;
+    const double gL = tfac * (ga * (A.P - pself) + gs * pself);
+    const double gD = nu0p * vth;
+    const double a = SQRTLN2 * gL / gD;
+    const double ku = SQRTLN2 / gD;
+    const double Sp = S * SQRTLN2PI / gD;
+    double cut;
+    if (A.cut_kind == HELK_CUT_ABS) cut = A.cut_value;
+    else if (A.cut_kind == HELK_CUT_LORENTZ) cut = fmin(A.cut_value * gL, A.cut_cap);
+    else cut = INFINITY;
+    double lo, hi;
+    if (A.cut_kind == HELK_CUT_NONE) {
+      lo = 0.0;
+      hi = (double)(A.ngrid - 1);
+    } else {
+      lo = ceil((nu0p - cut - A.nu_min) / A.dnu);
+      hi = floor((nu0p + cut - A.nu_min) / A.dnu);
+      if (lo < 0.0) lo = 0.0;
+      if (hi > (double)(A.ngrid - 1)) hi = (double)(A.ngrid - 1);
+      if (lo > (double)A.ngrid) lo = (double)A.ngrid;
+      if (hi < -1.0) hi = -1.0;
+    }
+    LineRec64 r;
+    r.nu0p = nu0p;
+    r.ku = ku;
+    r.a = a;
+    r.a2 = a * a;
+    r.Sp = Sp;
+    r.ilo = (int32_t)lo;
+    r.ihi = (int32_t)hi;
+    // Algorithm 916 per-line factors (only reachable when a < 10)
+    if (a < 10.0) {
+      r.erfcx_a = erfcx(a);
+      double s1 = 0.0;
+      for (int k = 0; k < A916_S1_TERMS; ++k) {
+        double nh = (double)(k + 1) * A916_H;
+        s1 += c_exp_nh2[k] / (nh * nh + a * a);
+      }
+      r.sig1 = s1;
+    } else {
+      r.erfcx_a = 0.0;
+      r.sig1 = 0.0;
+    }
+    rec[l] = r;
+    // reference index of the unshifted centre: non-decreasing in list order
+    double ck = floor((v0 - A.nu_min) / A.dnu);
+    if (ck < -4.0e15) ck = -4.0e15;
+    if (ck > 4.0e15) ck = 4.0e15;
+    ckey[l] = ck;
+    if (r.ihi >= r.ilo) {
+      evals += (unsigned long long)(r.ihi - r.ilo + 1);
+      long long c0 = (long long)ck;
+      long long h1 = c0 - r.ilo, h2 = (long long)r.ihi - c0;
+      long long hw = h1 > h2 ? h1 : h2;
+      if (hw > wmax) wmax = hw;
+      unsigned long long sb = (unsigned long long)__double_as_longlong(Sp);
+      if (sb > spmax) spmax = sb;
+    }
+  }
+  // warp-aggregate then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_down_sync(0xffffffffu, evals, o);
+    long long w2 = __shfl_down_sync(0xffffffffu, wmax, o);
+    if (w2 > wmax) wmax = w2;
+    unsigned long long s2 = __shfl_down_sync(0xffffffffu, spmax, o);
+    if (s2 > spmax) spmax = s2;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (evals) atomicAdd(&st->evals, evals);
+    if (wmax >= 0) atomicMax(&st->wmax, wmax);
+    if (spmax) atomicMax(&st->spmax_bits, spmax);
+  }
+}
+
+cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double q_ratio,
+                            const helk_cutoff &cut, const helk_grid &g, int precision) {
+  (void)precision;
+  const int64_t n = c->nlines;
+  if (n <= 0) return cudaSuccess;
+  PrepArgs A{T, P, mass, q_ratio, cut.kind, cut.value, cut.cap, g.nu_min, g.dnu, g.n};
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  k_lineprep<<<blocks, 256, 0, c->stream>>>(
+      n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair, c->has_gself ? c->gself : nullptr,
+      c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr, A, c->rec64, c->ckey,
+      c->stats);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- tile map --
+// Lines overlapping grid tile [A, B) have their reference index in
+// [A - W, B - 1 + W], W = max half-width of any window: a contiguous range
+// of the nu0-ordered list, found by two binary searches.
+__global__ void k_tilemap(int64_t nlines, const double *__restrict__ ckey, int64_t ngrid, int tile,
+                          int64_t ntiles, const DevStats *__restrict__ st, int32_t *tlo,
+                          int32_t *thi) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  long long W = st->wmax;
+  if (W < 0) {  // no line has a non-empty window
+    tlo[t] = 0;
+    thi[t] = 0;
+    return;
+  }
+  double A = (double)(t * tile);
+  double B = (double)((t + 1) * tile < ngrid ? (t + 1) * tile : ngrid);
+  double klo = A - (double)W, khi = B - 1.0 + (double)W;
+  int64_t lo = 0, hi = nlines;  // first index with ckey >= klo
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (ckey[mid] < klo) lo = mid + 1; else hi = mid;
+  }
+  int64_t first = lo;
+  lo = first; hi = nlines;      // first index with ckey > khi
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (ckey[mid] <= khi) lo = mid + 1; else hi = mid;
+  }
+  tlo[t] = (int32_t)first;
+  thi[t] = (int32_t)lo;
+}
+
+cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t ntiles) {
+  int blocks = (int)((ntiles + 127) / 128);
+  k_tilemap<<<blocks, 128, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->stats,
+                                           c->tile_lo, c->tile_hi);
+  return cudaGetLastError();
+}
+
+}  // namespace helk

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libhelk.so (include/helk.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions carry the C names; ``Context`` wraps them for torch
+tensors (device memory and streams come from PyTorch).  There is no CPU
+fallback: if the library cannot be loaded, importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhelk.so")
+
+HELK_OK = 0
+HELK_ERR_INVALID_ARG = -1
+HELK_ERR_OOM = -2
+HELK_ERR_CUDA = -3
+HELK_ERR_STATE = -4
+HELK_ERR_TIMEOUT = -5
+HELK_ERR_UNSUPPORTED = -6
+STATUS_NAMES = {0: "HELK_OK", -1: "HELK_ERR_INVALID_ARG", -2: "HELK_ERR_OOM", -3: "HELK_ERR_CUDA",
+                -4: "HELK_ERR_STATE", -5: "HELK_ERR_TIMEOUT", -6: "HELK_ERR_UNSUPPORTED"}
+
+HELK_CUT_ABS, HELK_CUT_LORENTZ, HELK_CUT_NONE = 0, 1, 2
+HELK_PREC_F64, HELK_PREC_F32_KAHAN = 0, 1
+
+
+class helk_grid(ctypes.Structure):
+    _fields_ = [("nu_min", ctypes.c_double), ("dnu", ctypes.c_double), ("n", ctypes.c_int64)]
+
+
+class helk_cutoff(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("cap", ctypes.c_double)]
+
+
+class helk_lines(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in
+                ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")]
+
+
+class helk_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("accumulate", ctypes.c_int32),
+                ("weight", ctypes.c_double), ("q_ratio", ctypes.c_double),
+                ("count_regions", ctypes.c_int32)]
+
+
+LINE_FIELDS = ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")
+
+# (name, restype, argtypes) of every exported entry point of include/helk.h
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+SIGNATURES = [
+    ("helk_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    ("helk_destroy", None, [_P]),
+    ("helk_last_error", ctypes.c_char_p, [_P]),
+    ("helk_set_stream", ctypes.c_int, [_P, _P]),
+    ("helk_sync", ctypes.c_int, [_P]),
+    ("helk_lines_upload", ctypes.c_int, [_P, ctypes.POINTER(helk_lines), _I64, _I32]),
+    ("helk_opacity", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(helk_cutoff),
+                                    ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts), _P]),
+    ("helk_opacity_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), _P]),
+    ("helk_kdist", ctypes.c_int, [_P, _P, _I64, _I32, _I32, _D, _P, _P, _I32, _P]),
+    ("helk_set_profiling", ctypes.c_int, [_P, _I32]),
+    ("helk_stage_times", ctypes.c_int, [_P, _P, _P]),
+]
+HELK_NSTAGES = 4
+STAGE_NAMES = ("lineprep", "voigt", "kdist", "setup")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libhelk.so is not built (run __graft_entry__.build() or "
+                          "python paper_1503_03806_gb300/build.py); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class HelkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+# ----------------------------------------------- C-named thin wrappers ---
+def helk_create(device=0, stream=None):
+    h = _P()
+    st = lib.helk_create(ctypes.byref(h), int(device), stream)
+    if st != HELK_OK:
+        raise HelkError(st, "helk_create failed")
+    return h
+
+
+def helk_destroy(ctx):
+    lib.helk_destroy(ctx)
+
+
+def helk_last_error(ctx):
+    s = lib.helk_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def _check(ctx, st):
+    if st != HELK_OK:
+        raise HelkError(st, helk_last_error(ctx))
+    return st
+
+
+def helk_set_stream(ctx, stream):
+    return _check(ctx, lib.helk_set_stream(ctx, stream))
+
+
+def helk_sync(ctx):
+    return _check(ctx, lib.helk_sync(ctx))
+
+
+def helk_lines_upload(ctx, lines_struct, n, on_device):
+    return lib.helk_lines_upload(ctx, ctypes.byref(lines_struct), int(n), int(on_device))
+
+
+def helk_opacity(ctx, T, P, mass, cut, grid, opts, kappa_ptr):
+    return lib.helk_opacity(ctx, float(T), float(P), float(mass), ctypes.byref(cut),
+                            ctypes.byref(grid), None if opts is None else ctypes.byref(opts),
+                            kappa_ptr)
+
+
+def helk_opacity_stats(ctx, with_regions=False):
+    ev = _I64(0)
+    reg = np.zeros(4, dtype=np.int64)
+    st = lib.helk_opacity_stats(ctx, ctypes.byref(ev),
+                                reg.ctypes.data_as(_P) if with_regions else None)
+    _check(ctx, st)
+    return int(ev.value), (reg if with_regions else None)
+
+
+def helk_kdist(ctx, kappa_ptr, n, nbins, ncheb, kappa_floor, coeffs_ptr, mean_ptr, out_on_host,
+               kg_ptr):
+    return lib.helk_kdist(ctx, kappa_ptr, int(n), int(nbins), int(ncheb), float(kappa_floor),
+                          coeffs_ptr, mean_ptr, int(out_on_host), kg_ptr)
+
+
+def helk_set_profiling(ctx, on):
+    return _check(ctx, lib.helk_set_profiling(ctx, int(bool(on))))
+
+
+def helk_stage_times(ctx):
+    ms = np.zeros(HELK_NSTAGES)
+    cnt = np.zeros(HELK_NSTAGES, dtype=np.int64)
+    _check(ctx, lib.helk_stage_times(ctx, ms.ctypes.data_as(_P), cnt.ctypes.data_as(_P)))
+    return {n: (float(ms[i]), int(cnt[i])) for i, n in enumerate(STAGE_NAMES)}
+
+
+# -------------------------------------------------------------- Context --
+def _cut(cut):
+    """cut: ("abs", C) | ("lorentz", multiple, cap) | ("none",)"""
+    kind = cut[0]
+    if kind == "abs":
+        return helk_cutoff(HELK_CUT_ABS, float(cut[1]), 0.0)
+    if kind == "lorentz":
+        return helk_cutoff(HELK_CUT_LORENTZ, float(cut[1]), float(cut[2]))
+    if kind == "none":
+        return helk_cutoff(HELK_CUT_NONE, 0.0, 0.0)
+    raise ValueError("unknown cutoff %r" % (cut,))
+
+
+class Context:
+    """A libhelk context bound to one CUDA device and (optionally) a torch
+    stream.  Tensors passed in must live on that device."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self._stream = stream
+        sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self.h = helk_create(self.device.index or 0, sp)
+        self.nlines = 0
+
+    def close(self):
+        if self.h:
+            helk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        helk_set_stream(self.h, None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+
+    def sync(self):
+        helk_sync(self.h)
+
+    # lines: dict of numpy arrays (host) or torch cuda tensors (device)
+    def upload(self, lines):
+        torch = self.torch
+        keep = {}
+        on_device = None
+        n = None
+        s = helk_lines()
+        for k in LINE_FIELDS:
+            v = lines.get(k)
+            if v is None:
+                continue
+            if isinstance(v, torch.Tensor):
+                dev = v.is_cuda
+                v = v.contiguous().to(torch.float64)
+                ptr = v.data_ptr()
+            else:
+                dev = False
+                v = np.ascontiguousarray(v, dtype=np.float64)
+                ptr = v.ctypes.data
+            if on_device is None:
+                on_device = dev
+            elif on_device != dev:
+                raise ValueError("all line fields must be on the same side (host or device)")
+            keep[k] = v
+            setattr(s, k, ptr)
+            n = v.shape[0] if n is None else n
+            if v.shape[0] != n:
+                raise ValueError("line fields differ in length")
+        _check(self.h, helk_lines_upload(self.h, s, n or 0, 1 if on_device else 0))
+        self.nlines = n or 0
+
+    def opacity(self, T, P, mass, cut, grid, out=None, precision=HELK_PREC_F64, accumulate=False,
+                weight=1.0, q_ratio=1.0, count_regions=False):
+        """grid = (nu_min, dnu, n).  Returns the kappa tensor (float64)."""
+        torch = self.torch
+        g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
+        if out is None:
+            out = torch.empty(int(grid[2]), dtype=torch.float64, device=self.device)
+        assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous()
+        o = helk_opts(int(precision), int(bool(accumulate)), float(weight), float(q_ratio),
+                      int(bool(count_regions)))
+        _check(self.h, helk_opacity(self.h, T, P, mass, _cut(cut), g, o, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def set_profiling(self, on):
+        helk_set_profiling(self.h, on)
+
+    def stage_times(self):
+        return helk_stage_times(self.h)
+
+    def stats(self, with_regions=False):
+        return helk_opacity_stats(self.h, with_regions)
+
+    def kdist(self, kappa, nbins, ncheb=20, kappa_floor=1e-250, want_sorted=False, on_host=False):
+        """Returns (coeffs[nbins, ncheb], mean[nbins], sorted or None)."""
+        torch = self.torch
+        n = int(kappa.shape[0])
+        kg = torch.empty_like(kappa) if want_sorted else None
+        if on_host:
+            coef = np.empty((nbins, ncheb))
+            mean = np.empty(nbins)
+            cp, mp = coef.ctypes.data, mean.ctypes.data
+        else:
+            coef = torch.empty((nbins, ncheb), dtype=torch.float64, device=self.device)
+            mean = torch.empty(nbins, dtype=torch.float64, device=self.device)
+            cp, mp = coef.data_ptr(), mean.data_ptr()
+        _check(self.h, helk_kdist(self.h, ctypes.c_void_p(kappa.data_ptr()), n, nbins, ncheb, kappa_floor,
+                                  ctypes.c_void_p(cp), ctypes.c_void_p(mp), 1 if on_host else 0,
+                                  None if kg is None else ctypes.c_void_p(kg.data_ptr())))
+        return coef, mean, kg
