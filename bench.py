@@ -35,13 +35,15 @@ L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic floating-point operations per evaluation (add/sub/mul/div = 1,
 # fma = 2), per method, as written in the kernels' formulas:
-#   GH1  u, r^2, one division, accumulate                     -> 6
-#   GH3  u, r^2, u-+t, d1, d2, d1+d2, d1 d2, num, den, /, *, + -> 19
-#   916  33 per evaluation + 10 per series term
-FLOPS_GH1, FLOPS_GH3, FLOPS_916_EVAL, FLOPS_916_TERM = 6, 19, 33, 10
+#   FP64 GH1  u, r^2, one division, accumulate                      -> 6
+#   FP64 GH3  u, r^2, u-+t, d1, d2, d1+d2, d1 d2, num, den, /, *, + -> 19
+#   FP64 916  33 per evaluation + 10 per series term
+#   FP32 forms add the grid offset (1) and replace the accumulate by the
+#   4 additions of the Kahan step: GH1 10, GH3 23, 916 37 + 10 per term.
+FLOPS = {"f64": (6, 19, 33, 10), "f32": (10, 23, 37, 10)}
 # FP64 pipe of GB300: 2 FP64 FMA / clock / SM (1.25 TFLOP/s nominal at the
-# 2.07 GHz maximum clock over 152 SMs).
-FP64_FMA_PER_CLK_SM = 2
+# 2.07 GHz maximum clock over 152 SMs); FP32: 128 FMA lanes / SM.
+FMA_PER_CLK_SM = {"f64": 2, "f32": 128}
 
 
 def workload_desc(w):
@@ -219,34 +221,40 @@ def run_ours(args):
     grid = (w["nu_min"], w["dnu"], w["ngrid"])
     nbins, ncheb = w["nbins"], w["ncheb"]
     lines = synth.workload_lines(WORKLOAD)
-    prec = helk.HELK_PREC_F64
+    PREC = {"f64": helk.HELK_PREC_F64, "f32": helk.HELK_PREC_F32_KAHAN}
+    peaks = measured_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
 
     ctx = helk.Context(local_rank)
     ctx.upload(lines)
     kappa = torch.empty(grid[2], dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    # work of one step (exact counts from the counting variant of the kernel)
-    ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec, count_regions=True)
-    evals, reg = ctx.stats(with_regions=True)
-    flops = (reg[2] * FLOPS_GH1 + reg[1] * FLOPS_GH3 + reg[0] * FLOPS_916_EVAL
-             + reg[3] * FLOPS_916_TERM)
+    def measure(form, clocks=False):
+        prec = PREC[form]
+        # work of one step (exact counts from the counting variant)
+        ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec, count_regions=True)
+        evals, reg = ctx.stats(with_regions=True)
+        f = FLOPS[form]
+        flops = int(reg[2] * f[0] + reg[1] * f[1] + reg[0] * f[2] + reg[3] * f[3])
 
-    def step():
-        ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec)
-        ctx.kdist(kappa, nbins, ncheb)
+        def step():
+            ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec)
+            ctx.kdist(kappa, nbins, ncheb)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ctx.set_profiling(True)
-    with Clocks(local_rank) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        clk = Clocks(local_rank) if clocks else None
+        if clk:
+            clk.__enter__()
         t0 = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()                      # L2 flush, outside the timed events
@@ -255,29 +263,60 @@ def run_ours(args):
             ends[i].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    if dist:
-        dist.barrier()
-    stage = ctx.stage_times()
-    ctx.set_profiling(False)
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_step = sum(ms) / len(ms)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * evals / (ms_step * 1e-3)
+        if clk:
+            clk.__exit__()
+        if dist:
+            dist.barrier()
+        stage = ctx.stage_times()
+        ctx.set_profiling(False)
+        ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        ms_step = sum(ms) / len(ms)
+        if dist:
+            t = torch.tensor([ms_step], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_step = float(t.item())
+        voigt_ms, voigt_n = stage["voigt"]
+        voigt_s = voigt_ms / max(1, voigt_n) * 1e-3
+        peak = FMA_PER_CLK_SM[form] * 2 * nsm * max_mhz * 1e6 / 1e12
+        achieved = flops / voigt_s / 1e12
+        src = os.path.join(ROOT, "paper_1503_03806_gb300", "csrc", "k_voigt.cu")
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": traffic_from_profile(src, os.path.join(ROOT, "profiles",
+                                                                  "voigt_%s_medium.txt" % form)),
+                "kernel": "k_voigt_" + form,
+                "peak_basis": "%s pipe: %d FMA/clk/SM x %d SMs x %.0f MHz max clock (derived)"
+                              % (form.upper(), FMA_PER_CLK_SM[form], nsm, max_mhz),
+                "flops_per_launch": flops, "voigt_ms_per_launch": voigt_s * 1e3}
+        return {"form": form, "evals": evals, "reg": [int(x) for x in reg], "ms_step": ms_step,
+                "value": world * evals / (ms_step * 1e-3), "roofline": roof, "wall": wall,
+                "stages": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
+                "clocks": clk.summary() if clk else None}
 
-    # end to end through the C ABI from pinned host memory
+    r64 = measure("f64")
+    k64 = kappa.clone()
+    r32 = measure("f32", clocks=True)
+    # accuracy of the FP32 form on this workload, against the FP64 form
+    # (itself held to the FP64 oracle at 1e-9 by the tests)
+    g = kappa.view(nbins, -1)
+    r = k64.view(nbins, -1)
+    sel = r > 1e-8 * r.max(dim=1, keepdim=True).values
+    err32 = float(((g - r).abs() / r)[sel].max().item())
+    clocks = r32["clocks"]
+    if clocks and clocks.get("sm_mhz"):
+        for rr in (r64, r32):
+            rr["roofline"]["frac_at_median_clock"] = rr["roofline"]["frac"] * max_mhz / clocks["sm_mhz"]
+
+    # end to end through the C ABI from pinned host memory (FP32 form)
     e2e = None
     if not args.no_e2e:
         pinned = {k: torch.from_numpy(v).pin_memory() for k, v in lines.items()}
         h2d = sum(v.numel() * 8 for v in pinned.values())
-        coef_h = np.empty((nbins, ncheb))
-        d2h = coef_h.nbytes + nbins * 8
+        d2h = nbins * ncheb * 8 + nbins * 8
 
         def e2e_step():
             ctx.upload(pinned)
-            ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec)
+            ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=PREC["f32"])
             ctx.kdist(kappa, nbins, ncheb, on_host=True)
 
         for _ in range(max(1, args.warmup)):
@@ -296,26 +335,8 @@ def run_ours(args):
             t = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        e2e = {"value": world * evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": world * r32["evals"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
-
-    peaks = measured_peaks()
-    clocks = clk.summary()
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    peak64 = FP64_FMA_PER_CLK_SM * 2 * nsm * max_mhz * 1e6 / 1e12
-    voigt_ms, voigt_n = stage["voigt"]
-    voigt_avg_s = voigt_ms / max(1, voigt_n) * 1e-3
-    achieved = flops / voigt_avg_s / 1e12
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_1503_03806_gb300", "csrc", "k_voigt.cu"),
-                                   os.path.join(ROOT, "profiles", "voigt_f64_medium.txt"))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": traffic, "kernel": "k_voigt_f64",
-                "peak_basis": "FP64 pipe, %d FMA/clk/SM x %d SMs x %.0f MHz (derived)"
-                              % (FP64_FMA_PER_CLK_SM, nsm, max_mhz),
-                "flops_per_launch": flops}
-    if clocks and clocks.get("sm_mhz"):
-        roofline["frac_at_median_clock"] = achieved / (peak64 * clocks["sm_mhz"] / max_mhz)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -323,24 +344,50 @@ def run_ours(args):
         ev_c, dt_c, nbs = oracle_sample(w, lines, 10.0, cores)
         cpu = {"value": ev_c / dt_c, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d contiguous k-bins (%d grid points, all overlapping lines): opacity + "
-                         "sort + fit, %.1f s" % (nbs, nbs * (grid[2] // nbins), dt_c)}
+                         "sort + fit, FP64, %.1f s" % (nbs, nbs * (grid[2] // nbins), dt_c)}
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": workload_desc(w), "precision": "fp64",
+        reg = r32["reg"]
+        out = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 (Voigt, Kahan) / f64 (k-tables)", "data": "synthetic",
+               "config": {"workload": workload_desc(w), "form": "FP32 Voigt + Kahan, FP64 k-tables",
                           "l2": "flushed between steps (256 MB write)",
-                          "evals_per_step": evals,
-                          "evals_by_method": {"alg916": int(reg[0]), "gh3": int(reg[1]),
-                                              "gh1": int(reg[2])}},
-               "stages_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
-               "wall_s_timed": wall, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clocks, "gpu_launches": 4 * args.steps}
+                          "evals_per_step": r32["evals"],
+                          "evals_by_method": {"alg916": reg[0], "gh3": reg[1], "gh1": reg[2]}},
+               "rel_err_f32_vs_f64": err32,
+               "stages_ms_per_step": r32["stages"],
+               "roofline": r32["roofline"], "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": 5 * args.steps,
+               "fp64": {"value": r64["value"], "ms_per_step": r64["ms_step"],
+                        "stages_ms_per_step": r64["stages"], "roofline": r64["roofline"],
+                        "gpu_launches": 4 * args.steps},
+               "speedup_f32_vs_f64": r32["value"] / r64["value"]}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_profile_case(form):
+    """Short fixed run for profilers: upload the workload, then two passes of
+    opacity (FP32 or FP64 form) + k-tables (the first is a warm-up)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1503_03806_gb300 import helk, synth
+    w = synth.WORKLOADS[WORKLOAD]
+    prec = helk.HELK_PREC_F32_KAHAN if form == "f32" else helk.HELK_PREC_F64
+    ctx = helk.Context(0)
+    ctx.upload(synth.workload_lines(WORKLOAD))
+    kappa = torch.empty(w["ngrid"], dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ctx.opacity(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], (w["nu_min"], w["dnu"], w["ngrid"]),
+                    out=kappa, precision=prec)
+        ctx.kdist(kappa, w["nbins"], w["ncheb"])
+    ctx.sync()
+    ctx.close()
 
 
 def main():
@@ -351,8 +398,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["f32", "f64"], default=None,
+                    help="run a short fixed case for ncu and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

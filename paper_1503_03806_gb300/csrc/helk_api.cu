@@ -259,8 +259,6 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   c->err.clear();
   const helk_opts o = opts ? *opts : default_opts();
   HELK_TRY(check_condition(c, T, P, mass, cut, g, o));
-  if (o.precision != HELK_PREC_F64)
-    return set_err(c, HELK_ERR_UNSUPPORTED, "opacity: precision not built");
   if (!c->nu0) return set_err(c, HELK_ERR_STATE, "opacity: no line list uploaded");
   HELK_TRY(bind_device(c));
   double *kappa = kappa_out;
@@ -271,7 +269,11 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   const int64_t nl = c->nlines > 0 ? c->nlines : 1;
   HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
   HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, nl * 8, "line keys"));
-  const int tile = voigt_tile_points(o.precision);
+  const bool f32 = o.precision == HELK_PREC_F32_KAHAN;
+  if (f32)
+    HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
+                        "FP32 line records"));
+  const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
   const int64_t ntiles = (g->n + tile - 1) / tile;
   if (ntiles > c->tile_cap) {
     if (c->tile_lo) cudaFree(c->tile_lo);
@@ -288,10 +290,11 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   if (c->nlines > 0) {
     stage_begin(c, HELK_STAGE_LINEPREP);
     HELK_TRY(cuda_check(c, launch_lineprep(c, T, P, mass, o.q_ratio, *cut, *g, o.precision), "lineprep"));
+    if (f32) HELK_TRY(cuda_check(c, launch_pack32(c, *g), "pack32"));
     HELK_TRY(cuda_check(c, launch_tilemap(c, *g, tile, ntiles), "tilemap"));
     stage_end(c, HELK_STAGE_LINEPREP);
     stage_begin(c, HELK_STAGE_VOIGT);
-    HELK_TRY(cuda_check(c, launch_voigt(c, *g, o, kappa, ntiles), "voigt"));
+    HELK_TRY(cuda_check(c, launch_voigt(c, *g, o, kappa, tile, ntiles), "voigt"));
     stage_end(c, HELK_STAGE_VOIGT);
   } else if (!o.accumulate) {
     HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));

@@ -79,7 +79,9 @@ struct DevStats {
   int err_flags;                    // ERRF_*
   int bad_lines;                    // validation failures at upload
   int unsorted;                     // upload: nu0 not ordered
-  int pad;
+  int scale_exp;                    // FP32 form: strengths scaled by 2^-scale_exp
+  unsigned int tile_counter;        // reserved for dynamic tile scheduling
+  int pad2;
 };
 enum { ERRF_TIMEOUT = 1 };
 
@@ -103,7 +105,7 @@ struct helk_ctx {
   helk::LineRec32 *rec32 = nullptr;
   double *ckey = nullptr;
   int64_t ckey_cap = 0;
-  int64_t rec_cap = 0;
+  int64_t rec_cap = 0, rec32_cap = 0;
   int32_t *tile_lo = nullptr, *tile_hi = nullptr;
   int64_t tile_cap = 0;
   helk::DevStats *stats = nullptr;      // device
@@ -194,11 +196,15 @@ cudaError_t launch_validate_lines(helk_ctx *c, int64_t n);
 cudaError_t launch_sort_lines(helk_ctx *c, int64_t n);  // orders SoA by nu0
 cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double q_ratio,
                             const helk_cutoff &cut, const helk_grid &g, int precision);
+cudaError_t launch_pack32(helk_ctx *c, const helk_grid &g);
 cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t ntiles);
 // k_voigt.cu
-int voigt_tile_points(int precision);
+// Tile length (points per CTA) for a grid of n points: a multiple of the
+// kernel's block size chosen so that the tiles fill whole waves of resident
+// CTAs.
+int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n);
 cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, double *kappa,
-                         int64_t ntiles);
+                         int tile_len, int64_t ntiles);
 // k_kdist.cu
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,

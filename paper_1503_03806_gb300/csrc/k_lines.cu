@@ -352,6 +352,50 @@ cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------- FP32 line records --
+// From the FP64 records: strengths scaled by 2^-E (E from the largest S' of
+// the call, so every scaled term is <= 1 and the FP32 range covers 38
+// decades below it); the centre as the integer grid index c plus the FP32
+// offset phi = (nu0' - nu_c) ku, so that u_i = (i - c) beta - phi keeps full
+// relative precision near the line centre.
+__global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64, double nu_min, double dnu,
+                         DevStats *st, LineRec32 *__restrict__ r32) {
+  const double spmax = __longlong_as_double((long long)st->spmax_bits);
+  const int E = spmax > 0.0 ? ilogb(spmax) + 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->scale_exp = E;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const LineRec64 r = r64[l];
+    LineRec32 q;
+    double cf = rint((r.nu0p - nu_min) / dnu);
+    if (cf < -1.0e9) cf = -1.0e9;
+    if (cf > 1.0e9) cf = 1.0e9;
+    q.c = (int32_t)cf;
+    q.ilo = r.ilo;
+    q.ihi = r.ihi;
+    q.phi_k = (float)((r.nu0p - (nu_min + cf * dnu)) * r.ku);
+    q.beta = (float)(dnu * r.ku);
+    q.a = (float)r.a;
+    q.a2 = (float)r.a2;
+    const double sp = ldexp(r.Sp, -E);
+    q.P1 = (float)(sp * r.a * INV_SQRTPI);
+    q.P3 = (float)(sp * r.a * (SQRTPI / 6.0) / PI);
+    q.Sp = (float)sp;
+    q.erfcx_a = (float)r.erfcx_a;
+    q.sig1 = (float)r.sig1;
+    r32[l] = q;
+  }
+}
+
+cudaError_t launch_pack32(helk_ctx *c, const helk_grid &g) {
+  const int64_t n = c->nlines;
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  k_pack32<<<blocks, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->stats, c->rec32);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- tile map --
 // Lines overlapping grid tile [A, B) have their reference index in
 // [A - W, B - 1 + W], W = max half-width of any window: a contiguous range

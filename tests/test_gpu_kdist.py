@@ -1,11 +1,17 @@
 """GPU parity of the k-distribution stage (Sec. 2.2, 2.6).
 
 Sorted values: bit-exact against the oracle's library sort on identical
-input.  Chebyshev coefficients: the GPU solves the normal equations with a
-shared Cholesky factor, the oracle uses Householder QR; both are backward
-stable for this well-conditioned basis (cond(A) < 10), so the coefficient
-vectors agree to ~1e-13 of their norm; the bar is 1e-9 of max|c| per bin.
-Bin means: 1e-12 relative (summation order only).
+input.  Chebyshev coefficients: the GPU applies the pseudo-inverse of the
+design matrix shared by all bins (one Householder QR per bin size), the
+oracle runs a Householder QR per bin; both are backward stable and the basis
+is well conditioned at the workloads' bin sizes (cond(A) ~ 5), so the
+coefficient vectors agree to ~1e-13 of their norm; the bar is 1e-9 of max|c|
+per bin.
+Bin means: 1e-12 relative (summation order only).  When N_b is close to
+n_cheb the least-squares problem itself becomes ill-conditioned (uniform
+abscissae: cond(A) = 2.9e8 for 32 points and 32 coefficients), and any two
+backward-stable solvers then differ by up to ~eps cond(A); the bar becomes
+max(1e-9, 100 eps cond(A)).
 """
 import numpy as np
 import pytest
@@ -42,7 +48,11 @@ def check_kdist(ctx, kappa, nbins, ncheb, floor=1e-250, on_host=False):
     assert np.array_equal(srt.view(np.uint64), s_or.view(np.uint64)), "sorted values differ"
     scale = np.max(np.abs(c_or), axis=1, keepdims=True)
     err = np.max(np.abs(coef - c_or) / scale)
-    assert err <= RTOL_COEF, err
+    nb = kappa.shape[0] // nbins
+    g = (np.arange(nb) + 0.5) / nb
+    cond = np.linalg.cond(np.polynomial.chebyshev.chebvander(2 * g - 1, ncheb - 1))
+    tol = max(RTOL_COEF, 100 * np.finfo(float).eps * cond)
+    assert err <= tol, (err, tol, cond)
     assert_rel(mean, m_or, 1e-12, "bin mean")
     return err
 

@@ -59,8 +59,8 @@ def test_lorentz_cutoff_all_fields(ctx):
 
 
 def test_no_cutoff_full_profile(ctx):
-    lines = synth.random_lines(40, 103, 0.0, 30.0)
-    case = Case(900.0, 0.2, 16.0, (0.0, 0.005, 6000 + 11), ("none",))
+    lines = synth.random_lines(40, 103, 1000.0, 1030.0)
+    case = Case(900.0, 0.2, 16.0, (1000.0, 0.005, 6000 + 11), ("none",))
     k, ev, reg, ko, evo, rego = run_both(ctx, lines, case)
     assert ev == evo == 40 * 6011 and np.array_equal(reg[:3], rego)
     assert rego[0] > 0 and rego[1] > 0 and rego[2] > 0
