@@ -180,6 +180,39 @@ enum { HELK_STAGE_LINEPREP = 0, HELK_STAGE_VOIGT = 1, HELK_STAGE_KDIST = 2,
 helk_status helk_set_profiling(helk_ctx *ctx, int32_t on);
 helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
 
+/* Allocation-free k-distribution tables (no counterpart in the paper; an
+ * interface addition).  Same computation and outputs as helk_kdist with
+ * device-pointer outputs, for callers that must not allocate device memory:
+ * code that runs while a CUDA graph is being captured (cudaMalloc/cudaFree
+ * are not stream-ordered and break or invalidate the capture), code inside a
+ * framework whose pool allocator owns all device memory, and latency-bound
+ * loops that cannot afford the device-wide synchronisation of cudaFree.
+ *
+ * It needs no context and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Its scratch (the pseudo-inverse of the Chebyshev basis
+ * and its QR work array) lives in a fixed 6 MiB device array that every GPU
+ * loading the library holds until the process exits.  Limits: N_b = n/nbins
+ * <= 12288 points per bin and 1 <= ncheb <= 32 (the bin sort then runs in
+ * shared memory); larger requests return HELK_ERR_INVALID_ARG, as do null
+ * kappa/coeffs, n % nbins != 0 and kappa_floor <= 0.  Runs on the current
+ * CUDA device and on `stream` (a cudaStream_t, NULL = legacy default).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents: the
+ * pseudo-inverse for the last (N_b, ncheb) is reused when the next call on
+ * that device has the same sizes and recomputed otherwise; no part of it
+ * needs to start at zero.  Calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on the array: order them on one stream
+ * or synchronise between them.
+ *
+ * kappa: device, n doubles.  coeffs: device, nbins*ncheb doubles.  mean,
+ * kg_out: device or NULL, as in helk_kdist. */
+helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t nbins,
+                              int32_t ncheb, double kappa_floor,
+                              double *coeffs, double *mean, double *kg_out,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "helk_internal.cuh"
 
 namespace helk {
@@ -313,4 +315,84 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ allocation-free variant --
+// Scratch of helk_kdist_static in a file-scope device array instead of
+// cudaMalloc'd memory: the pseudo-inverse of the Chebyshev basis (N_b x
+// n_cheb doubles) followed by the Householder work array of the same size.
+// Bins are limited to KDIST_STATIC_NB_MAX points (their sort then runs in
+// shared memory, so no other scratch is needed) and n_cheb to NCHEB_MAX:
+// 2 x 12288 x 32 x 8 B = 6 MiB, held by every device that loads the library
+// until the process exits.
+constexpr int64_t KDIST_STATIC_NB_MAX = 12288;
+constexpr int64_t KDIST_STATIC_PINV = KDIST_STATIC_NB_MAX * NCHEB_MAX;
+static __device__ __align__(256) double g_kdist_scratch[2 * KDIST_STATIC_PINV];
+
+namespace {
+constexpr int KDIST_STATIC_MAX_DEVICES = 64;
+struct StaticScratch {
+  double *ptr = nullptr;  // device address of g_kdist_scratch on this device
+  int64_t nb = 0;         // sizes whose pseudo-inverse the array holds
+  int ncheb = 0;
+};
+StaticScratch g_static[KDIST_STATIC_MAX_DEVICES];
+std::mutex g_static_mu;
+}  // namespace
+
 }  // namespace helk
+
+extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t nbins,
+                                         int32_t ncheb, double kappa_floor, double *coeffs,
+                                         double *mean, double *kg_out, void *stream) {
+  using namespace helk;
+  if (!kappa || !coeffs) return HELK_ERR_INVALID_ARG;
+  if (n <= 0 || nbins <= 0 || n % nbins) return HELK_ERR_INVALID_ARG;
+  const int64_t nb = n / nbins;
+  if (nb > KDIST_STATIC_NB_MAX || ncheb < 1 || ncheb > NCHEB_MAX || ncheb > nb)
+    return HELK_ERR_INVALID_ARG;
+  if (!(kappa_floor > 0.0) || !isfinite(kappa_floor)) return HELK_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= KDIST_STATIC_MAX_DEVICES) {
+    cudaGetLastError();
+    return HELK_ERR_CUDA;
+  }
+  int smem_optin = 0;
+  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return HELK_ERR_CUDA;
+  const size_t smem = (size_t)nb * 16;
+  if ((int64_t)smem + 26 * 1024 > smem_optin) return HELK_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *ptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticScratch &S = g_static[dev];
+    if (!S.ptr) {
+      // once per device, with that device current: the array's device address
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_kdist_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return HELK_ERR_CUDA;
+      }
+      S.ptr = (double *)p;
+    }
+    ptr = S.ptr;
+    if (S.nb != nb || S.ncheb != ncheb) {
+      k_pinv<<<1, PI_THREADS, 0, st>>>(nb, ncheb, ptr + KDIST_STATIC_PINV, nullptr, ptr);
+      if (cudaGetLastError() != cudaSuccess) {
+        S.nb = 0;
+        S.ncheb = 0;
+        return HELK_ERR_CUDA;
+      }
+      S.nb = nb;
+      S.ncheb = ncheb;
+    }
+  }
+  if (cudaFuncSetAttribute(k_kdist_bin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return HELK_ERR_CUDA;
+  }
+  k_kdist_bin<true><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor, ptr, nullptr,
+                                                     nullptr, coeffs, mean, kg_out);
+  return cudaGetLastError() == cudaSuccess ? HELK_OK : HELK_ERR_CUDA;
+}
+

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("helk_kdist", ctypes.c_int, [_P, _P, _I64, _I32, _I32, _D, _P, _P, _I32, _P]),
     ("helk_set_profiling", ctypes.c_int, [_P, _I32]),
     ("helk_stage_times", ctypes.c_int, [_P, _P, _P]),
+    ("helk_kdist_static", ctypes.c_int, [_P, _I64, _I32, _I32, _D, _P, _P, _P, _P]),
 ]
 HELK_NSTAGES = 4
 STAGE_NAMES = ("lineprep", "voigt", "kdist", "setup")
