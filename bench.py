@@ -233,6 +233,7 @@ def run_ours(args):
 
     def measure(form, clocks=False):
         prec = PREC[form]
+        tile = ctx.autotune(T, P, mass, cut, grid, precision=prec)   # one-time setup
         # work of one step (exact counts from the counting variant)
         ctx.opacity(T, P, mass, cut, grid, out=kappa, precision=prec, count_regions=True)
         evals, reg = ctx.stats(with_regions=True)
@@ -287,7 +288,8 @@ def run_ours(args):
                 "kernel": "k_voigt_" + form,
                 "peak_basis": "%s pipe: %d FMA/clk/SM x %d SMs x %.0f MHz max clock (derived)"
                               % (form.upper(), FMA_PER_CLK_SM[form], nsm, max_mhz),
-                "flops_per_launch": flops, "voigt_ms_per_launch": voigt_s * 1e3}
+                "flops_per_launch": flops, "voigt_ms_per_launch": voigt_s * 1e3,
+                "tile_points": tile}
         return {"form": form, "evals": evals, "reg": [int(x) for x in reg], "ms_step": ms_step,
                 "value": world * evals / (ms_step * 1e-3), "roofline": roof, "wall": wall,
                 "stages": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},

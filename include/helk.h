@@ -80,9 +80,17 @@ typedef struct {
  *   gamma_self self-broadening coefficient; NULL: = gamma_air
  *   n_coll     temperature exponent; NULL: 0.5
  *   delta      pressure shift [cm^-1/atm]; NULL: 0
- * All values must be finite, S0 >= 0, gamma_* >= 0. */
+ *   mass       molecular mass of the line's species [amu]; NULL: the mass
+ *              passed to helk_opacity
+ *   weight     abundance (mixing ratio) of the line's species; multiplies S;
+ *              NULL: 1.  With mass and weight one list holds several species,
+ *              whose opacities are then added before the k-distribution
+ *              (Sec. 2.1)
+ * All values must be finite, nu0 > 0, S0 >= 0, gamma_* >= 0, mass > 0,
+ * weight >= 0. */
 typedef struct {
     const double *nu0, *S0, *E_lower, *gamma_air, *gamma_self, *n_coll, *delta;
+    const double *mass, *weight;
 } helk_lines;
 
 /* Arithmetic of the Voigt stage.
@@ -164,6 +172,19 @@ helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
                        int32_t nbins, int32_t ncheb, double kappa_floor,
                        double *coeffs, double *mean, int32_t out_on_host,
                        double *kg_out);
+
+/* Autotuner of the Voigt kernel's tile shape.  Runs the line preparation of
+ * this condition once, then times every built tile shape (points per CTA)
+ * of opts->precision on it (three launches each, CUDA events on the context
+ * stream) and keeps the fastest for later helk_opacity calls with the same
+ * precision and grid size; other sizes fall back to the built-in choice
+ * (tiles filling whole waves of resident CTAs).  *tile_out (optional)
+ * receives the chosen points per tile.  Overwrites the context's own
+ * opacity buffer; synchronises. */
+helk_status helk_autotune(helk_ctx *ctx, double T, double P_atm,
+                          double mass_amu, const helk_cutoff *cut,
+                          const helk_grid *grid, const helk_opts *opts,
+                          int32_t *tile_out);
 
 /* Stage timing (tracing).  With profiling on, the library records a CUDA
  * event pair on the context stream around each stage it launches:

@@ -57,7 +57,7 @@ def lib():
         L.or_gh1.argtypes = [_d, _d]
         L.or_voigt_H.restype = _d
         L.or_voigt_H.argtypes = [_d, _d, _p]
-        line_args = [_i64] + [_p] * 7 + [_d, _d, _d, _d, ctypes.c_int, _d, _d,
+        line_args = [_i64] + [_p] * 9 + [_d, _d, _d, _d, ctypes.c_int, _d, _d,
                                          _d, _d, _i64]
         L.or_lineprep.restype = ctypes.c_int
         L.or_lineprep.argtypes = line_args + [_p] * 9
@@ -131,12 +131,14 @@ class Condition:
                 self.cut_value, self.cut_cap, self.nu_min, self.dnu, self.ngrid]
 
 
+LINE_FIELDS = ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta", "mass",
+               "weight")
+
+
 def _line_ptrs(lines):
-    keep = {k: _f64(lines.get(k)) for k in
-            ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")}
+    keep = {k: _f64(lines.get(k)) for k in LINE_FIELDS}
     n = int(keep["nu0"].shape[0])
-    ptrs = [_ptr(keep[k]) for k in
-            ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")]
+    ptrs = [_ptr(keep[k]) for k in LINE_FIELDS]
     return n, ptrs, keep
 
 

@@ -154,8 +154,11 @@ double or_voigt_H(double a, double u, int *region)
  * ===================================================================== */
 
 typedef struct {
-    /* inputs, SoA; any pointer but nu0/S0/gamma_air may be NULL */
+    /* inputs, SoA; any pointer but nu0/S0/gamma_air may be NULL.
+     * mass (amu) and weight (abundance) per line let one list hold several
+     * species (Sec. 2.1: mixing ratios applied before the k-distribution). */
     const double *nu0, *S0, *E_lower, *gamma_air, *gamma_self, *n_coll, *delta;
+    const double *mass, *weight;
 } or_lines;
 
 /* Per-line record.  nu0p = shifted centre, Sp = S sqrt(ln2/pi)/Gamma_D,
@@ -174,7 +177,9 @@ typedef struct {
  *    applied only when E'' is given; q_ratio = Q(T0)/Q(T) is an input.
  *  - Lorentz HWHM    Gamma_L = (T0/T)^n [a_air (P - Pself) + a_self Pself]/P0,
  *                    Pself = P/2, natural width dropped        (Sec. 2.3)
- *  - Doppler HWHM    Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c  (Sec. 2.4)
+ *  - Doppler HWHM    Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c  (Sec. 2.4),
+ *                    m = the line's own mass when the list carries one
+ *  - abundance       S is multiplied by the line's weight when given
  *  - cutoff C and window: inclusive |nu_i - nu0'| <= C        (Sec. 2.5)
  */
 static void or_prep_one(const or_lines *L, int64_t l, double T, double P,
@@ -201,12 +206,14 @@ static void or_prep_one(const or_lines *L, int64_t l, double T, double P,
             stim = OR_T0 / T;                  /* limit nu0 -> 0 */
         S = S * q_ratio * boltz * stim;
     }
+    if (L->weight) S = S * L->weight[l];
     r->S = S;
 
     tfac  = (ncoll == 0.5) ? sqrt(OR_T0 / T) : pow(OR_T0 / T, ncoll);
     pself = 0.5 * P;
     r->gL = tfac * (g_air * (P - pself) + g_slf * pself);
 
+    if (L->mass) mass = L->mass[l];
     vth   = sqrt(2.0 * OR_LN2 * OR_KB * T / (mass * OR_AMU)) / OR_CLIGHT;
     r->gD = r->nu0p * vth;
 
@@ -233,13 +240,14 @@ static void or_prep_one(const or_lines *L, int64_t l, double T, double P,
 int or_lineprep(int64_t n, const double *nu0, const double *S0,
                 const double *E_lower, const double *gamma_air,
                 const double *gamma_self, const double *n_coll,
-                const double *delta, double T, double P, double mass,
+                const double *delta, const double *mass_l, const double *weight_l,
+                double T, double P, double mass,
                 double q_ratio, int cut_kind, double cut_value, double cut_cap,
                 double nu_min, double dnu, int64_t ngrid,
                 double *nu0p, double *S, double *Sp, double *ku, double *a,
                 double *gD, double *gL, int64_t *ilo, int64_t *ihi)
 {
-    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta };
+    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta, mass_l, weight_l };
     int64_t l;
     for (l = 0; l < n; ++l) {
         or_rec r;
@@ -309,13 +317,14 @@ static void *or_opacity_chunk(void *arg)
 int or_opacity(int64_t n, const double *nu0, const double *S0,
                const double *E_lower, const double *gamma_air,
                const double *gamma_self, const double *n_coll,
-               const double *delta, double T, double P, double mass,
+               const double *delta, const double *mass_l, const double *weight_l,
+               double T, double P, double mass,
                double q_ratio, int cut_kind, double cut_value, double cut_cap,
                double nu_min, double dnu, int64_t ngrid, double weight,
                int accumulate, double *kappa, int nthreads,
                int64_t *evals_out, int64_t *region_out)
 {
-    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta };
+    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta, mass_l, weight_l };
     or_rec *rec;
     or_chunk *ch;
     pthread_t *th;
@@ -358,13 +367,14 @@ int or_opacity(int64_t n, const double *nu0, const double *S0,
 int or_opacity_points(int64_t n, const double *nu0, const double *S0,
                       const double *E_lower, const double *gamma_air,
                       const double *gamma_self, const double *n_coll,
-                      const double *delta, double T, double P, double mass,
+                      const double *delta, const double *mass_l,
+                      const double *weight_l, double T, double P, double mass,
                       double q_ratio, int cut_kind, double cut_value,
                       double cut_cap, double nu_min, double dnu, int64_t ngrid,
                       int64_t npts, const int64_t *idx, double *kappa_pts,
                       int64_t *evals_out)
 {
-    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta };
+    or_lines L = { nu0, S0, E_lower, gamma_air, gamma_self, n_coll, delta, mass_l, weight_l };
     int64_t l, p, ev = 0;
     for (p = 0; p < npts; ++p) kappa_pts[p] = 0.0;
     for (l = 0; l < n; ++l) {

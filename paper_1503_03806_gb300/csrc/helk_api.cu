@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -138,7 +139,7 @@ void helk_destroy(helk_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
-                  c->delta, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
+                  c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
                   c->mean_dev, c->tmp};
   for (void *p : bufs)
@@ -178,8 +179,10 @@ helk_status helk_lines_upload(helk_ctx *c, const helk_lines *L, int64_t n, int32
     return set_err(c, HELK_ERR_INVALID_ARG, "lines_upload: nu0, S0 and gamma_air are required");
   HELK_TRY(bind_device(c));
   const int64_t bytes = (n > 0 ? n : 1) * 8;
-  double **dst[7] = {&c->nu0, &c->S0, &c->El, &c->gair, &c->gself, &c->ncoll, &c->delta};
-  const double *src[7] = {L->nu0, L->S0, L->E_lower, L->gamma_air, L->gamma_self, L->n_coll, L->delta};
+  double **dst[9] = {&c->nu0, &c->S0, &c->El, &c->gair, &c->gself, &c->ncoll, &c->delta, &c->lmass,
+                     &c->lweight};
+  const double *src[9] = {L->nu0, L->S0, L->E_lower, L->gamma_air, L->gamma_self, L->n_coll, L->delta,
+                          L->mass, L->weight};
   if (bytes > c->lines_cap) {
     HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "lines_upload"));
     for (auto d : dst)
@@ -193,7 +196,7 @@ helk_status helk_lines_upload(helk_ctx *c, const helk_lines *L, int64_t n, int32
   }
   c->nlines = 0;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int f = 0; f < 7; ++f)
+  for (int f = 0; f < 9; ++f)
     if (src[f] && n > 0)
       HELK_TRY(cuda_check(c, cudaMemcpyAsync(*dst[f], src[f], (size_t)(n * 8), kind, c->stream),
                           "lines_upload copy"));
@@ -201,6 +204,8 @@ helk_status helk_lines_upload(helk_ctx *c, const helk_lines *L, int64_t n, int32
   c->has_gself = L->gamma_self != nullptr;
   c->has_ncoll = L->n_coll != nullptr;
   c->has_delta = L->delta != nullptr;
+  c->has_mass = L->mass != nullptr;
+  c->has_weight = L->weight != nullptr;
   HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, sizeof(DevStats), c->stream), "lines_upload"));
   HELK_TRY(cuda_check(c, launch_validate_lines(c, n), "validate lines"));
   HELK_TRY(cuda_check(c, cudaMemcpyAsync(c->stats_host, c->stats, sizeof(DevStats),
@@ -253,6 +258,39 @@ static helk_opts default_opts() {
   return o;
 }
 
+static helk_status ensure_tiles(helk_ctx *c, int64_t ntiles) {
+  if (ntiles <= c->tile_cap) return HELK_OK;
+  if (c->tile_lo) cudaFree(c->tile_lo);
+  if (c->tile_hi) cudaFree(c->tile_hi);
+  c->tile_lo = c->tile_hi = nullptr;
+  c->tile_cap = 0;
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_lo, (size_t)ntiles * 4), "tile map"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_hi, (size_t)ntiles * 4), "tile map"));
+  c->tile_cap = ntiles;
+  return HELK_OK;
+}
+
+// Line buffers of one condition, statistics reset, line preparation (and
+// the FP32 records).
+static helk_status prepare_lines(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
+                                 const helk_grid *g, const helk_opts &o) {
+  const int64_t nl = c->nlines > 0 ? c->nlines : 1;
+  HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
+  HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, nl * 8, "line keys"));
+  const bool f32 = o.precision == HELK_PREC_F32_KAHAN;
+  if (f32)
+    HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
+                        "FP32 line records"));
+  // reset per-call statistics (keep error flags)
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, offsetof(DevStats, err_flags), c->stream), "stats"));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->wmax, 0xFF, sizeof(long long), c->stream), "stats"));
+  if (c->nlines > 0) {
+    HELK_TRY(cuda_check(c, launch_lineprep(c, T, P, mass, o.q_ratio, *cut, *g, o.precision), "lineprep"));
+    if (f32) HELK_TRY(cuda_check(c, launch_pack32(c, *g), "pack32"));
+  }
+  return HELK_OK;
+}
+
 helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
                          const helk_grid *g, const helk_opts *opts, double *kappa_out) {
   if (!c) return HELK_ERR_INVALID_ARG;
@@ -266,42 +304,82 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
     HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
     kappa = c->kappa;
   }
-  const int64_t nl = c->nlines > 0 ? c->nlines : 1;
-  HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
-  HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, nl * 8, "line keys"));
-  const bool f32 = o.precision == HELK_PREC_F32_KAHAN;
-  if (f32)
-    HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
-                        "FP32 line records"));
   const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
   const int64_t ntiles = (g->n + tile - 1) / tile;
-  if (ntiles > c->tile_cap) {
-    if (c->tile_lo) cudaFree(c->tile_lo);
-    if (c->tile_hi) cudaFree(c->tile_hi);
-    c->tile_lo = c->tile_hi = nullptr;
-    c->tile_cap = 0;
-    HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_lo, (size_t)ntiles * 4), "tile map"));
-    HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->tile_hi, (size_t)ntiles * 4), "tile map"));
-    c->tile_cap = ntiles;
-  }
-  // reset per-call statistics (keep error flags)
-  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, offsetof(DevStats, err_flags), c->stream), "stats"));
-  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->wmax, 0xFF, sizeof(long long), c->stream), "stats"));
+  HELK_TRY(ensure_tiles(c, ntiles));
+  stage_begin(c, HELK_STAGE_LINEPREP);
+  HELK_TRY(prepare_lines(c, T, P, mass, cut, g, o));
   if (c->nlines > 0) {
-    stage_begin(c, HELK_STAGE_LINEPREP);
-    HELK_TRY(cuda_check(c, launch_lineprep(c, T, P, mass, o.q_ratio, *cut, *g, o.precision), "lineprep"));
-    if (f32) HELK_TRY(cuda_check(c, launch_pack32(c, *g), "pack32"));
     HELK_TRY(cuda_check(c, launch_tilemap(c, *g, tile, ntiles), "tilemap"));
     stage_end(c, HELK_STAGE_LINEPREP);
     stage_begin(c, HELK_STAGE_VOIGT);
     HELK_TRY(cuda_check(c, launch_voigt(c, *g, o, kappa, tile, ntiles), "voigt"));
     stage_end(c, HELK_STAGE_VOIGT);
-  } else if (!o.accumulate) {
-    HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
+  } else {
+    stage_end(c, HELK_STAGE_LINEPREP);
+    if (!o.accumulate)
+      HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
   }
   c->last_n = g->n;
   c->have_opacity = (kappa == c->kappa);
   c->last_counted_regions = o.count_regions != 0;
+  return HELK_OK;
+}
+
+helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
+                          const helk_grid *g, const helk_opts *opts, int32_t *tile_out) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  helk_opts o = opts ? *opts : default_opts();
+  o.count_regions = 0;
+  o.accumulate = 0;
+  HELK_TRY(check_condition(c, T, P, mass, cut, g, o));
+  if (!c->nu0 || c->nlines <= 0) return set_err(c, HELK_ERR_STATE, "autotune: no line list uploaded");
+  HELK_TRY(bind_device(c));
+  HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
+  const int prec = o.precision == HELK_PREC_F32_KAHAN ? 1 : 0;
+  c->tuned_tile[prec] = 0;  // time the candidates, not the previous choice
+  int cand[8];
+  const int ncand = voigt_tile_candidates(o.precision, cand, 8);
+  int64_t max_tiles = 0;
+  for (int i = 0; i < ncand; ++i) max_tiles = std::max(max_tiles, (g->n + cand[i] - 1) / cand[i]);
+  HELK_TRY(ensure_tiles(c, max_tiles));
+  HELK_TRY(prepare_lines(c, T, P, mass, cut, g, o));
+  cudaEvent_t e0, e1;
+  HELK_TRY(cuda_check(c, cudaEventCreate(&e0), "autotune"));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_check(c, cudaErrorUnknown, "autotune");
+  }
+  double best_ms = 1e300;
+  int best = cand[0];
+  helk_status st = HELK_OK;
+  for (int i = 0; i < ncand && st == HELK_OK; ++i) {
+    const int64_t ntiles = (g->n + cand[i] - 1) / cand[i];
+    st = cuda_check(c, launch_tilemap(c, *g, cand[i], ntiles), "autotune");
+    if (st == HELK_OK) st = cuda_check(c, launch_voigt(c, *g, o, c->kappa, cand[i], ntiles), "autotune");
+    float ms = 0.f, tot = 0.f;
+    const int reps = 3;
+    if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e0, c->stream), "autotune");
+    for (int r = 0; r < reps && st == HELK_OK; ++r)
+      st = cuda_check(c, launch_voigt(c, *g, o, c->kappa, cand[i], ntiles), "autotune");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e1, c->stream), "autotune");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventSynchronize(e1), "autotune");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "autotune");
+    tot = ms / reps;
+    if (st == HELK_OK && tot < best_ms) {
+      best_ms = tot;
+      best = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HELK_TRY(st);
+  HELK_TRY(helk_sync(c));
+  c->tuned_tile[prec] = best;
+  c->tuned_n[prec] = g->n;
+  c->have_opacity = false;
+  if (tile_out) *tile_out = best;
   return HELK_OK;
 }
 

@@ -97,8 +97,10 @@ struct helk_ctx {
   // line list (sorted SoA)
   int64_t nlines = 0;
   bool has_E = false, has_gself = false, has_ncoll = false, has_delta = false;
+  bool has_mass = false, has_weight = false;
   double *nu0 = nullptr, *S0 = nullptr, *El = nullptr, *gair = nullptr,
-         *gself = nullptr, *ncoll = nullptr, *delta = nullptr;
+         *gself = nullptr, *ncoll = nullptr, *delta = nullptr, *lmass = nullptr,
+         *lweight = nullptr;
   int64_t lines_cap = 0;
   // per-call scratch
   helk::LineRec64 *rec64 = nullptr;
@@ -127,6 +129,10 @@ struct helk_ctx {
   // generic upload scratch
   void *tmp = nullptr;
   int64_t tmp_cap = 0;
+  // autotuned Voigt tile length per precision (0 = heuristic), valid for
+  // grids of tuned_n points
+  int tuned_tile[2] = {0, 0};
+  int64_t tuned_n[2] = {0, 0};
   // stage timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev[HELK_NSTAGES];  // start/end pairs
@@ -203,6 +209,8 @@ cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t nt
 // kernel's block size chosen so that the tiles fill whole waves of resident
 // CTAs.
 int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n);
+// Tile lengths the autotuner times (points per CTA).
+int voigt_tile_candidates(int precision, int *out, int max);
 cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, double *kappa,
                          int tile_len, int64_t ntiles);
 // k_kdist.cu

@@ -27,16 +27,20 @@ __constant__ double c_exp_nh2[A916_S1_TERMS] = {
 __global__ void k_validate(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
                            const double *__restrict__ El, const double *__restrict__ gair,
                            const double *__restrict__ gself, const double *__restrict__ ncoll,
-                           const double *__restrict__ delta, DevStats *st) {
+                           const double *__restrict__ delta, const double *__restrict__ lmass,
+                           const double *__restrict__ lweight, DevStats *st) {
   int bad = 0, unsorted = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     double v = nu0[l];
-    bool ok = isfinite(v) && isfinite(S0[l]) && S0[l] >= 0.0 && isfinite(gair[l]) && gair[l] >= 0.0;
+    bool ok = isfinite(v) && v > 0.0 && isfinite(S0[l]) && S0[l] >= 0.0 && isfinite(gair[l]) &&
+              gair[l] >= 0.0;
     if (El) ok = ok && isfinite(El[l]);
     if (gself) ok = ok && isfinite(gself[l]) && gself[l] >= 0.0;
     if (ncoll) ok = ok && isfinite(ncoll[l]);
     if (delta) ok = ok && isfinite(delta[l]);
+    if (lmass) ok = ok && isfinite(lmass[l]) && lmass[l] > 0.0;
+    if (lweight) ok = ok && isfinite(lweight[l]) && lweight[l] >= 0.0;
     bad += !ok;
     if (l + 1 < n && nu0[l + 1] < v) unsorted = 1;
   }
@@ -51,7 +55,9 @@ cudaError_t launch_validate_lines(helk_ctx *c, int64_t n) {
   k_validate<<<blocks, 256, 0, c->stream>>>(n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
                                             c->has_gself ? c->gself : nullptr,
                                             c->has_ncoll ? c->ncoll : nullptr,
-                                            c->has_delta ? c->delta : nullptr, c->stats);
+                                            c->has_delta ? c->delta : nullptr,
+                                            c->has_mass ? c->lmass : nullptr,
+                                            c->has_weight ? c->lweight : nullptr, c->stats);
   return cudaGetLastError();
 }
 
@@ -210,10 +216,11 @@ cudaError_t launch_sort_lines(helk_ctx *c, int64_t n) {
     unsigned long long *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
   }
-  double *fields[7] = {c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
+  double *fields[9] = {c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
                        c->has_gself ? c->gself : nullptr, c->has_ncoll ? c->ncoll : nullptr,
-                       c->has_delta ? c->delta : nullptr};
-  for (int f = 0; f < 7; ++f) {
+                       c->has_delta ? c->delta : nullptr, c->has_mass ? c->lmass : nullptr,
+                       c->has_weight ? c->lweight : nullptr};
+  for (int f = 0; f < 9; ++f) {
     if (!fields[f]) continue;
     k_gather<<<gb, 256, 0, c->stream>>>(n, va, fields[f], dtmp);
     cudaError_t e = cudaMemcpyAsync(fields[f], dtmp, n * 8, cudaMemcpyDeviceToDevice, c->stream);
@@ -241,7 +248,8 @@ struct PrepArgs {
 __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
                            const double *__restrict__ El, const double *__restrict__ gair,
                            const double *__restrict__ gself, const double *__restrict__ ncoll,
-                           const double *__restrict__ delta, PrepArgs A, LineRec64 *__restrict__ rec,
+                           const double *__restrict__ delta, const double *__restrict__ lmass,
+                           const double *__restrict__ lweight, PrepArgs A, LineRec64 *__restrict__ rec,
                            double *__restrict__ ckey, DevStats *st) {
   unsigned long long evals = 0;
   long long wmax = -1;
@@ -262,10 +270,11 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
       const double stim = v0 > 0.0 ? expm1(-C2 * v0 / A.T) / expm1(-C2 * v0 / T0) : T0 / A.T;
       S = S * A.q_ratio * boltz * stim;
     }
+    if (lweight) S = S * lweight[l];
     const double tfac = (nc == 0.5) ? sqrt(T0 / A.T) : pow(T0 / A.T, nc);
     const double pself = 0.5 * A.P;
     const double gL = tfac * (ga * (A.P - pself) + gs * pself);
-    const double gD = nu0p * vth;
+    const double gD = nu0p * (lmass ? sqrt(2.0 * LN2 * KB * A.T / (lmass[l] * AMU)) / CLIGHT : vth);
     const double a = SQRTLN2 * gL / gD;
     const double ku = SQRTLN2 / gD;
     const double Sp = S * SQRTLN2PI / gD;
@@ -347,7 +356,8 @@ cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double
   if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
   k_lineprep<<<blocks, 256, 0, c->stream>>>(
       n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair, c->has_gself ? c->gself : nullptr,
-      c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr, A, c->rec64, c->ckey,
+      c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr,
+      c->has_mass ? c->lmass : nullptr, c->has_weight ? c->lweight : nullptr, A, c->rec64, c->ckey,
       c->stats);
   return cudaGetLastError();
 }

@@ -114,6 +114,19 @@ __device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, float si
   return K;
 }
 
+// Reciprocal of a double x >= 100: FP32 hardware seed (relative error
+// < 2^-22) refined by one Newton step, relative error < 1e-13 -- far inside
+// the 1e-9 budget of the FP64 form, at a fraction of the cost of an IEEE
+// division on the FP64 pipe.  Beyond the FP32 range the seed is 0 and the
+// division is done exactly.
+__device__ __forceinline__ double rcp64(double x) {
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)x));
+  if (rf == 0.0f) return 1.0 / x;
+  const double r = (double)rf;
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 // ------------------------------------------------------ line staging ----
 // Double-buffered bulk-copy pipeline over the line range [l0, l1).
 template <typename Rec, int LCH>
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(BLOCK)
       const bool full = (ilo <= base) && (ihi >= base + tile_len - 1);
       const double nu0p = L.nu0p, ku = L.ku, a = L.a, a2 = L.a2, Sp = L.Sp;
       const double P1 = Sp * a * INV_SQRTPI;           // GH1: (a/pi) sqrt(pi)
-      const double P3 = Sp * a * (SQRTPI / 6.0) / PI;  // GH3 outer weight
+      const double P3h = 2.0 * (Sp * a * (SQRTPI / 6.0) / PI);  // GH3 outer weight x 2
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (k >= nslot) break;
@@ -200,15 +213,14 @@ __global__ void __launch_bounds__(BLOCK)
           const double r2 = __dadd_rn(__dmul_rn(u, u), a2);
           double v;
           if (r2 >= R2_GH1) {
-            v = P1 / r2;
+            v = P1 * rcp64(r2);
             if (COUNT) cnt[2]++;
           } else if (r2 >= R2_GH3) {
-            // (a/pi)[w0/d0 + w1/d1 + w1/d2], w0 = 4 w1, one division
-            const double um = u - GH3_T, up = u + GH3_T;
-            const double d1 = um * um + a2, d2 = up * up + a2;
-            const double p = d1 * d2;
-            const double num = 4.0 * p + r2 * (d1 + d2);
-            v = P3 * (num / (r2 * p));
+            // (a w1/pi)[4/r2 + 2q/p], q = r2 + t^2, p = d1 d2 = q^2 - 4t^2u^2
+            const double q = r2 + 1.5;
+            const double p = fma(q, q, (u * u) * -6.0);
+            const double num = fma(2.0, p, r2 * q);
+            v = P3h * (num * rcp64(r2 * p));
             if (COUNT) cnt[1]++;
           } else {
             v = Sp * k916_f64(fabs(u), a, L.erfcx_a, L.sig1);
@@ -243,22 +255,72 @@ __global__ void __launch_bounds__(BLOCK)
 }
 
 // ------------------------------------------------------------ FP32 form --
-template <int BLOCK, int PPT, int LCH, bool COUNT>
+// Method classes of one (line, tile) pair.  |u| is monotone in |i - c| in
+// the FP32 arithmetic used per point (u = fma(d, beta, -phi) is correctly
+// rounded, so monotone in the exact integer d, and fma(u, u, a^2) is monotone
+// in |u|), so the extreme r^2 over the tile's covered points decide whether
+// every point of the pair uses the same method.  Pure pairs run a
+// branch-free loop over all slots (independent chains the compiler can
+// interleave); mixed pairs -- those containing a method boundary or the line
+// core -- decide per point.
+enum { CLS_GH1 = 0, CLS_GH3 = 1, CLS_MIXED = 2 };
+constexpr float F32_T1 = 1.2247448714f;     // GH3 node sqrt(3/2)
+constexpr float F32_T1SQ = 1.5f;            // its square
+constexpr int KAHAN_GROUP = 8;              // lines per compensated partial
+
+// Hardware reciprocal approximation (max relative error ~1 ulp); every
+// argument here is >= 100, far from the denormal range.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// 3-node Gauss-Hermite in the form (a w1/pi) [4/r2 + 2q/p] with
+// q = r2 + t^2 and p = d1 d2 = q^2 - 4 t^2 u^2 (no cancellation for r2 >= 100);
+// P3h = Sp a (sqrt(pi)/6)/pi * 2 folded per line.  Returns the term.
+__device__ __forceinline__ float gh3_term(float u, float r2, float P3h) {
+  const float q = r2 + F32_T1SQ;
+  const float m = (u * u) * (-4.0f * F32_T1SQ);
+  const float p = fmaf(q, q, m);
+  const float num = fmaf(2.0f, p, r2 * q);
+  return P3h * (num * fast_rcp(r2 * p));
+}
+
+template <int BLOCK, int NSLOT, int LCH, bool COUNT>
 __global__ void __launch_bounds__(BLOCK)
     k_voigt_f32(const LineRec32 *__restrict__ rec, const int32_t *__restrict__ tlo,
-                const int32_t *__restrict__ thi, int ngrid, int nslot, double weight,
-                int accumulate, double *__restrict__ kappa, DevStats *st) {
+                const int32_t *__restrict__ thi, int ngrid, double weight, int accumulate,
+                double *__restrict__ kappa, DevStats *st) {
+  // Warp w of the CTA owns the WSPAN consecutive points starting at
+  // base + w WSPAN; lane l holds points base + w WSPAN + 32 k + l.  Method
+  // classes are decided per (line, warp), so only the warps whose span holds
+  // a method boundary or the line core take the per-point path.
+  constexpr int TILE = BLOCK * NSLOT;
+  constexpr int WSPAN = 32 * NSLOT;
   __shared__ __align__(128) LineRec32 sl[2][LCH];
   __shared__ __align__(8) unsigned long long mbar[2];
-  const int tid = threadIdx.x;
-  const int tile_len = BLOCK * nslot;
-  const int base = blockIdx.x * tile_len;
-  float sum[PPT], comp[PPT];
+  const int lane = threadIdx.x & 31;
+  const int base = blockIdx.x * TILE;
+  const int wbase = base + (threadIdx.x >> 5) * WSPAN;
+  // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
+  // into part[k] (relative error <= 7 u) and Kahan-adds the partial into
+  // (sum, comp); total relative error < 6e-7.
+  float sum[NSLOT], comp[NSLOT], part[NSLOT];
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
+  for (int k = 0; k < NSLOT; ++k) {
     sum[k] = 0.0f;
     comp[k] = 0.0f;
+    part[k] = 0.0f;
   }
+  int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
   LineStager<LineRec32, LCH> stg;
   stg.init(sl, mbar, rec, tlo[blockIdx.x], thi[blockIdx.x]);
@@ -267,46 +329,98 @@ __global__ void __launch_bounds__(BLOCK)
     const int cnum = stg.count(ch);
     const LineRec32 *buf = sl[ch & 1];
     for (int j = 0; j < cnum; ++j) {
-      const LineRec32 &L = buf[j];
-      const int ilo = L.ilo, ihi = L.ihi;
-      if (ihi < base || ilo >= base + tile_len || ihi < ilo) continue;
-      const bool full = (ilo <= base) && (ihi >= base + tile_len - 1);
-      const float beta = L.beta, nphi = -L.phi_k, a2 = L.a2, P1 = L.P1, P3 = L.P3;
-      // (i - c) for this thread's first point; exact in FP32 (|i - c| < 2^24
-      // whenever the point is inside the window)
-      const float d0 = (float)(base + tid - L.c);
+      const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
+      const int lo = max(ilo, wbase), hi = min(ihi, wbase + WSPAN - 1);
+      if (lo > hi) continue;  // warp-uniform
+      if (++ngroup == KAHAN_GROUP) {
+        ngroup = 0;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (k >= nslot) break;
-        const int i = base + tid + k * BLOCK;
-        if (full || (i >= ilo && i <= ihi)) {
-          const float u = fmaf(d0 + (float)(k * BLOCK), beta, nphi);
-          const float r2 = fmaf(u, u, a2);
-          float v;
-          if (r2 >= 1.0e6f) {
-            v = __fdividef(P1, r2);
-            if (COUNT) cnt[2]++;
-          } else if (r2 >= 100.0f) {
-            const float um = u - 1.2247448714f, up = u + 1.2247448714f;
-            const float d1 = fmaf(um, um, a2), d2 = fmaf(up, up, a2);
-            const float p = d1 * d2;
-            const float num = fmaf(4.0f, p, r2 * (d1 + d2));
-            v = P3 * __fdividef(num, r2 * p);
-            if (COUNT) cnt[1]++;
-          } else {
-            v = L.Sp * k916_f32(fabsf(u), L.a, L.erfcx_a, L.sig1);
-            if (COUNT) {
-              int n0, n1;
-              a916_range(fabs((double)u), n0, n1);
-              cnt[0]++;
-              cnt[3] += (unsigned long long)(n1 - n0 + 1);
-            }
+        for (int k = 0; k < NSLOT; ++k) {
+          kahan_add(sum[k], comp[k], part[k]);
+          part[k] = 0.0f;
+        }
+      }
+      const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
+      // extreme r^2 over the warp's covered points [lo, hi]
+      const int dlo = lo - c, dhi = hi - c;
+      const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
+      const float un = fmaf((float)dnear, beta, nphi);
+      const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
+      const float r2near = fmaf(un, un, a2);
+      const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
+      const int cls = r2near >= 1.0e6f ? CLS_GH1
+                                       : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
+      const bool full = (lo == wbase) && (hi == wbase + WSPAN - 1);
+      // (i - c) of this lane's first point, exact in FP32
+      const float d0 = (float)(wbase + lane - c);
+      if (cls == CLS_GH1) {
+        const float P1 = buf[j].P1;
+        if (full) {
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            part[k] += P1 * fast_rcp(r2);
           }
-          // Kahan-compensated accumulation
-          const float yk = v - comp[k];
-          const float t = sum[k] + yk;
-          comp[k] = (t - sum[k]) - yk;
-          sum[k] = t;
+          if (COUNT) cnt[2] += NSLOT;
+        } else {
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const int i = wbase + lane + 32 * k;
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+            part[k] += in ? P1 * fast_rcp(r2) : 0.0f;
+            if (COUNT) cnt[2] += in;
+          }
+        }
+      } else if (cls == CLS_GH3) {
+        const float P3h = 2.0f * buf[j].P3;
+        if (full) {
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            part[k] += gh3_term(u, r2, P3h);
+          }
+          if (COUNT) cnt[1] += NSLOT;
+        } else {
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const int i = wbase + lane + 32 * k;
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+            part[k] += in ? gh3_term(u, r2, P3h) : 0.0f;
+            if (COUNT) cnt[1] += in;
+          }
+        }
+      } else {
+        const float P1 = buf[j].P1, P3h = 2.0f * buf[j].P3;
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+          const int i = wbase + lane + 32 * k;
+          if ((unsigned)(i - lo) <= (unsigned)(hi - lo)) {
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            float v;
+            if (r2 >= 1.0e6f) {
+              v = P1 * fast_rcp(r2);
+              if (COUNT) cnt[2]++;
+            } else if (r2 >= 100.0f) {
+              v = gh3_term(u, r2, P3h);
+              if (COUNT) cnt[1]++;
+            } else {
+              v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+              if (COUNT) {
+                int n0, n1;
+                a916_range(fabs((double)u), n0, n1);
+                cnt[0]++;
+                cnt[3] += (unsigned long long)(n1 - n0 + 1);
+              }
+            }
+            part[k] += v;
+          }
         }
       }
     }
@@ -314,9 +428,10 @@ __global__ void __launch_bounds__(BLOCK)
   }
   const double scale = ldexp(weight, st->scale_exp);
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int i = base + tid + k * BLOCK;
-    if (k < nslot && i < ngrid) {
+  for (int k = 0; k < NSLOT; ++k) {
+    kahan_add(sum[k], comp[k], part[k]);
+    const int i = wbase + lane + 32 * k;
+    if (i < ngrid) {
       const double v = scale * ((double)sum[k] - (double)comp[k]);
       kappa[i] = accumulate ? kappa[i] + v : v;
     }
@@ -325,14 +440,14 @@ __global__ void __launch_bounds__(BLOCK)
     for (int r = 0; r < 4; ++r) {
       unsigned long long v = cnt[r];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((tid & 31) == 0 && v) atomicAdd(&st->region[r], v);
+      if (lane == 0 && v) atomicAdd(&st->region[r], v);
     }
   }
 }
 
 // --------------------------------------------------------------- launch --
 constexpr int F64_BLOCK = 256, F64_PPT = 8, F64_LCH = 64;
-constexpr int F32_BLOCK = 256, F32_PPT = 16, F32_LCH = 128;
+constexpr int F32_BLOCK = 256, F32_LCH = 256;
 
 template <typename K>
 static int resident_ctas(helk_ctx *c, K kern, int block) {
@@ -344,17 +459,20 @@ static int resident_ctas(helk_ctx *c, K kern, int block) {
   return occ * c->num_sms;
 }
 
-// Pick nslot <= PPT so that ceil(n / (BLOCK nslot)) tiles fill whole waves
+// Pick nslot <= ppt so that ceil(n / (block nslot)) tiles fill whole waves
 // of `slots` resident CTAs as evenly as possible, preferring long tiles
 // (each (line, tile) pair has a fixed setup cost of about one slot).
+static double tile_score(int64_t n, int block, int p, int slots) {
+  const int64_t ntiles = (n + (int64_t)block * p - 1) / ((int64_t)block * p);
+  const double waves = (double)ntiles / slots;
+  return waves / ceil(waves) * p / (p + 1.0);
+}
+
 static int pick_nslot(int64_t n, int block, int ppt, int slots) {
   int best = ppt;
   double best_score = -1.0;
   for (int p = ppt; p >= 1; --p) {
-    const int64_t ntiles = (n + (int64_t)block * p - 1) / ((int64_t)block * p);
-    const double waves = (double)ntiles / slots;
-    const double eff = waves / ceil(waves);
-    const double score = eff * p / (p + 1.0);
+    const double score = tile_score(n, block, p, slots);
     if (score > best_score + 1e-9) {
       best_score = score;
       best = p;
@@ -363,11 +481,48 @@ static int pick_nslot(int64_t n, int block, int ppt, int slots) {
   return best;
 }
 
-int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n) {
+// FP32 tiles: NSLOT is a template parameter (no per-slot bounds test in the
+// hot loops); the instantiated choices are 8, 12 and 16 slots.
+#define HELK_F32_NSLOTS(X) X(8) X(12) X(16)
+
+template <int NS>
+static int f32_slots(helk_ctx *c, bool count) {
+  return count ? resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, true>, F32_BLOCK)
+               : resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, false>, F32_BLOCK);
+}
+
+int voigt_tile_candidates(int precision, int *out, int max) {
+  int n = 0;
   if (precision == HELK_PREC_F32_KAHAN) {
-    const int slots = count ? resident_ctas(c, k_voigt_f32<F32_BLOCK, F32_PPT, F32_LCH, true>, F32_BLOCK)
-                            : resident_ctas(c, k_voigt_f32<F32_BLOCK, F32_PPT, F32_LCH, false>, F32_BLOCK);
-    return F32_BLOCK * pick_nslot(n, F32_BLOCK, F32_PPT, slots);
+#define X(NS) \
+    if (n < max) out[n++] = F32_BLOCK * NS;
+    HELK_F32_NSLOTS(X)
+#undef X
+  } else {
+    const int f64_choices[] = {4, 6, 8};
+    for (int p : f64_choices)
+      if (n < max) out[n++] = F64_BLOCK * p;
+  }
+  return n;
+}
+
+int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n) {
+  const int prec = precision == HELK_PREC_F32_KAHAN ? 1 : 0;
+  if (!count && c->tuned_tile[prec] > 0 && c->tuned_n[prec] == n) return c->tuned_tile[prec];
+  if (precision == HELK_PREC_F32_KAHAN) {
+    int best = 16;
+    double best_score = -1.0;
+#define X(NS)                                                        \
+    {                                                                \
+      const double sc = tile_score(n, F32_BLOCK, NS, f32_slots<NS>(c, count)); \
+      if (sc > best_score + 1e-9) {                                  \
+        best_score = sc;                                             \
+        best = NS;                                                   \
+      }                                                              \
+    }
+    HELK_F32_NSLOTS(X)
+#undef X
+    return F32_BLOCK * best;
   }
   const int slots = count ? resident_ctas(c, k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true>, F64_BLOCK)
                           : resident_ctas(c, k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false>, F64_BLOCK);
@@ -378,24 +533,30 @@ cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, do
                          int tile_len, int64_t ntiles) {
   const unsigned grid = (unsigned)ntiles;
   if (o.precision == HELK_PREC_F32_KAHAN) {
-    const int nslot = tile_len / F32_BLOCK;
-    if (o.count_regions)
-      k_voigt_f32<F32_BLOCK, F32_PPT, F32_LCH, true><<<grid, F32_BLOCK, 0, c->stream>>>(
-          c->rec32, c->tile_lo, c->tile_hi, (int)g.n, nslot, o.weight, o.accumulate, kappa, c->stats);
-    else
-      k_voigt_f32<F32_BLOCK, F32_PPT, F32_LCH, false><<<grid, F32_BLOCK, 0, c->stream>>>(
-          c->rec32, c->tile_lo, c->tile_hi, (int)g.n, nslot, o.weight, o.accumulate, kappa, c->stats);
-  } else {
-    const int nslot = tile_len / F64_BLOCK;
-    if (o.count_regions)
-      k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true><<<grid, F64_BLOCK, 0, c->stream>>>(
-          c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
-          kappa, c->stats);
-    else
-      k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false><<<grid, F64_BLOCK, 0, c->stream>>>(
-          c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
-          kappa, c->stats);
+    const int ns = tile_len / F32_BLOCK;
+#define X(NS)                                                                                     \
+    if (ns == NS) {                                                                               \
+      if (o.count_regions)                                                                        \
+        k_voigt_f32<F32_BLOCK, NS, F32_LCH, true><<<grid, F32_BLOCK, 0, c->stream>>>(             \
+            c->rec32, c->tile_lo, c->tile_hi, (int)g.n, o.weight, o.accumulate, kappa, c->stats); \
+      else                                                                                        \
+        k_voigt_f32<F32_BLOCK, NS, F32_LCH, false><<<grid, F32_BLOCK, 0, c->stream>>>(            \
+            c->rec32, c->tile_lo, c->tile_hi, (int)g.n, o.weight, o.accumulate, kappa, c->stats); \
+      return cudaGetLastError();                                                                  \
+    }
+    HELK_F32_NSLOTS(X)
+#undef X
+    return cudaErrorInvalidValue;
   }
+  const int nslot = tile_len / F64_BLOCK;
+  if (o.count_regions)
+    k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true><<<grid, F64_BLOCK, 0, c->stream>>>(
+        c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
+        kappa, c->stats);
+  else
+    k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false><<<grid, F64_BLOCK, 0, c->stream>>>(
+        c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
+        kappa, c->stats);
   return cudaGetLastError();
 }
 

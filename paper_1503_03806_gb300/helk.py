@@ -37,7 +37,8 @@ class helk_cutoff(ctypes.Structure):
 
 class helk_lines(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")]
+                ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta", "mass",
+                 "weight")]
 
 
 class helk_opts(ctypes.Structure):
@@ -46,7 +47,8 @@ class helk_opts(ctypes.Structure):
                 ("count_regions", ctypes.c_int32)]
 
 
-LINE_FIELDS = ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta")
+LINE_FIELDS = ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta", "mass",
+               "weight")
 
 # (name, restype, argtypes) of every exported entry point of include/helk.h
 _P = ctypes.c_void_p
@@ -67,6 +69,9 @@ SIGNATURES = [
     ("helk_set_profiling", ctypes.c_int, [_P, _I32]),
     ("helk_stage_times", ctypes.c_int, [_P, _P, _P]),
     ("helk_kdist_static", ctypes.c_int, [_P, _I64, _I32, _I32, _D, _P, _P, _P, _P]),
+    ("helk_autotune", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(helk_cutoff),
+                                     ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
+                                     ctypes.POINTER(_I32)]),
 ]
 HELK_NSTAGES = 4
 STAGE_NAMES = ("lineprep", "voigt", "kdist", "setup")
@@ -248,6 +253,16 @@ class Context:
                       int(bool(count_regions)))
         _check(self.h, helk_opacity(self.h, T, P, mass, _cut(cut), g, o, ctypes.c_void_p(out.data_ptr())))
         return out
+
+    def autotune(self, T, P, mass, cut, grid, precision=HELK_PREC_F64, q_ratio=1.0):
+        """Time the built Voigt tile shapes on this condition; keep the
+        fastest for later calls with the same precision and grid size."""
+        g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
+        o = helk_opts(int(precision), 0, 1.0, float(q_ratio), 0)
+        t = _I32(0)
+        _check(self.h, lib.helk_autotune(self.h, float(T), float(P), float(mass), ctypes.byref(_cut(cut)),
+                                         ctypes.byref(g), ctypes.byref(o), ctypes.byref(t)))
+        return int(t.value)
 
     def set_profiling(self, on):
         helk_set_profiling(self.h, on)

@@ -41,7 +41,7 @@ def run_both(ctx, lines, case, count=True, **kw):
 
 @pytest.mark.parametrize("ngrid", [2048, 20000 + 123, 1])
 def test_random_lines_abs_cutoff(ctx, ngrid):
-    lines = synth.random_lines(500, 101, -1.0, 201.0)
+    lines = synth.random_lines(500, 101, 0.05, 201.0)
     case = Case(1500.0, 1.0, 18.0, (0.0, 0.01, ngrid), ("abs", 3.0))
     k, ev, reg, ko, evo, rego = run_both(ctx, lines, case)
     assert ev == evo
@@ -177,8 +177,9 @@ def test_invalid_arguments(ctx):
     with pytest.raises(helk.HelkError) as e:
         ctx.upload(bad_lines)
     assert e.value.status == helk.HELK_ERR_INVALID_ARG
-    nan_lines = dict(lines)
-    nan_lines["nu0"] = lines["nu0"].copy()
-    nan_lines["nu0"][0] = float("inf")
-    with pytest.raises(helk.HelkError):
-        ctx.upload(nan_lines)
+    for badval in (float("inf"), float("nan"), 0.0, -3.0):
+        nan_lines = dict(lines)
+        nan_lines["nu0"] = lines["nu0"].copy()
+        nan_lines["nu0"][0] = badval
+        with pytest.raises(helk.HelkError):
+            ctx.upload(nan_lines)

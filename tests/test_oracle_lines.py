@@ -171,3 +171,28 @@ def test_points_equal_full_grid():
     idx = np.array([0, 17, 555, 4321, 9999, 5000])
     kp, _ = oracle.opacity_points(lines, cond, idx)
     assert np.array_equal(kp, k[idx])
+
+
+def test_per_line_mass_and_weight():
+    # one list holding two species (Sec. 2.1: abundance-weighted opacities are
+    # added before the k-distribution)
+    A = synth.random_lines(150, 51, 0.0, 100.0)
+    B = synth.random_lines(120, 52, 0.0, 100.0)
+    cond = _small_cond(cut=4.0, ngrid=10000)
+    kA, _, _ = oracle.opacity(A, oracle.Condition(1500.0, 1.0, 18.0, 0.0, 0.01, 10000,
+                                                  oracle.CUT_ABS, 4.0))
+    kB, _, _ = oracle.opacity(B, oracle.Condition(1500.0, 1.0, 44.0, 0.0, 0.01, 10000,
+                                                  oracle.CUT_ABS, 4.0))
+    mix = {k: np.concatenate([A[k], B[k]]) for k in A}
+    mix["mass"] = np.concatenate([np.full(150, 18.0), np.full(120, 44.0)])
+    mix["weight"] = np.concatenate([np.full(150, 0.7), np.full(120, 0.3)])
+    kM, _, _ = oracle.opacity(mix, cond)
+    np.testing.assert_allclose(kM, 0.7 * kA + 0.3 * kB, rtol=1e-13, atol=0)
+    # Doppler width scales as m^-1/2
+    r = oracle.lineprep(mix, cond)
+    one = {k: v[:1] for k, v in A.items()}
+    one4 = dict(one, mass=np.array([72.0]))
+    g18 = oracle.lineprep(one, oracle.Condition(1500.0, 1.0, 18.0, 0.0, 0.01, 10))["gD"][0]
+    g72 = oracle.lineprep(one4, oracle.Condition(1500.0, 1.0, 18.0, 0.0, 0.01, 10))["gD"][0]
+    assert abs(g18 / g72 - 2.0) < 1e-15
+    assert np.all(r["gD"][:150] > 0)
