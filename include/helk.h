@@ -147,6 +147,31 @@ helk_status helk_opacity(helk_ctx *ctx, double T, double P_atm,
                          const helk_grid *grid, const helk_opts *opts,
                          double *kappa_out);
 
+/* Opacities of the uploaded lines at n_cond conditions (T[k], P_atm[k]) on
+ * one grid, in one persistent launch (Sec. 2.3-2.5; the paper's many (T, P)
+ * points).  kappa_out: device pointer to n_cond * grid->n doubles, row k =
+ * condition k (NULL: the context's buffer, read by helk_kdist with
+ * kappa == NULL and n = n_cond * grid->n -- the k-tables of all conditions
+ * then come from one helk_kdist call with n_cond * nbins bins).  q_ratio:
+ * per-condition Q(T0)/Q(T) or NULL (opts->q_ratio for all).  T, P, q_ratio
+ * are host arrays, read during the call.  The whole sequence is captured
+ * once per call shape (n_cond, line list, grid, cutoff, options, output
+ * pointer, tile shape) into a CUDA graph and replayed on later calls with the
+ * same shape; only the condition values change between replays.  The
+ * results equal those of n_cond helk_opacity calls bit for bit.  A call
+ * waits until the previous batch call has read its conditions. */
+helk_status helk_opacity_batch(helk_ctx *ctx, int32_t n_cond, const double *T,
+                               const double *P_atm, const double *q_ratio,
+                               double mass_amu, const helk_cutoff *cut,
+                               const helk_grid *grid, const helk_opts *opts,
+                               double *kappa_out);
+
+/* Evaluation counts of the first n_cond conditions of the last opacity call
+ * (n_evals[k]; region_counts[4k..4k+3] as in helk_opacity_stats when that call
+ * counted regions, else pass NULL).  Synchronises. */
+helk_status helk_opacity_batch_stats(helk_ctx *ctx, int32_t n_cond,
+                                     int64_t *n_evals, int64_t *region_counts);
+
 /* Statistics of the last helk_opacity: number of (line, grid point) Voigt
  * evaluations and, if region_counts != NULL (4 entries; the last opacity
  * must have run with count_regions), how many fell in each method
@@ -200,6 +225,21 @@ enum { HELK_STAGE_LINEPREP = 0, HELK_STAGE_VOIGT = 1, HELK_STAGE_KDIST = 2,
        HELK_STAGE_SETUP = 3, HELK_NSTAGES = 4 };
 helk_status helk_set_profiling(helk_ctx *ctx, int32_t on);
 helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
+
+/* Transmission of every bin for nm column masses m (Sec. 2.1, Eq. for T:
+ * T(m) = int_0^1 exp(-k(g) m) dg; the paper's "Transmission" stage).
+ *   sorted (device, nbins*nb doubles, e.g. kg_out of helk_kdist) or NULL:
+ *     direct[b*nm + i] = (1/nb) sum_j exp(-k_j m_i), the midpoint rule on
+ *     g_j = (j + 1/2)/nb; by Sec. 2.1 this equals the band-mean transmission
+ *     of the unsorted bin.
+ *   coeffs (device, nbins*ncheb) or NULL: fit[b*nm + i] by the midpoint rule
+ *     on ng points of the resampled k(g) = exp(sum_k c_k T_k(2g - 1)).
+ * m: host array of nm column masses (cm^2/molecule units inverse to kappa),
+ * finite and >= 0.  direct, fit: device arrays of nbins*nm doubles. */
+helk_status helk_transmission(helk_ctx *ctx, int32_t nbins, int64_t nb,
+                              const double *sorted, const double *coeffs,
+                              int32_t ncheb, int32_t ng, int32_t nm,
+                              const double *m, double *direct, double *fit);
 
 /* Allocation-free k-distribution tables (no counterpart in the paper; an
  * interface addition).  Same computation and outputs as helk_kdist with

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <new>
 #include <string>
 
@@ -138,6 +139,7 @@ void helk_destroy(helk_ctx *c) {
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->mass_col) cudaFree(c->mass_col);
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
                   c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
@@ -145,6 +147,14 @@ void helk_destroy(helk_ctx *c) {
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (c->stats_host) cudaFreeHost(c->stats_host);
+  if (c->cond_dev) cudaFree(c->cond_dev);
+  if (c->cstats) cudaFree(c->cstats);
+  if (c->cond_order) cudaFree(c->cond_order);
+  if (c->cond_host) cudaFreeHost(c->cond_host);
+  if (c->cstats_host) cudaFreeHost(c->cstats_host);
+  if (c->cond_ev) cudaEventDestroy(c->cond_ev);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int st = 0; st < HELK_NSTAGES; ++st)
     for (cudaEvent_t e : c->ev[st]) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
@@ -206,7 +216,8 @@ helk_status helk_lines_upload(helk_ctx *c, const helk_lines *L, int64_t n, int32
   c->has_delta = L->delta != nullptr;
   c->has_mass = L->mass != nullptr;
   c->has_weight = L->weight != nullptr;
-  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, sizeof(DevStats), c->stream), "lines_upload"));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->bad_lines, 0, 2 * sizeof(int), c->stream),
+                      "lines_upload"));
   HELK_TRY(cuda_check(c, launch_validate_lines(c, n), "validate lines"));
   HELK_TRY(cuda_check(c, cudaMemcpyAsync(c->stats_host, c->stats, sizeof(DevStats),
                                          cudaMemcpyDeviceToHost, c->stream),
@@ -270,24 +281,68 @@ static helk_status ensure_tiles(helk_ctx *c, int64_t ntiles) {
   return HELK_OK;
 }
 
-// Line buffers of one condition, statistics reset, line preparation (and
-// the FP32 records).
-static helk_status prepare_lines(helk_ctx *c, double T, double P, double mass, const helk_cutoff *cut,
-                                 const helk_grid *g, const helk_opts &o) {
-  const int64_t nl = c->nlines > 0 ? c->nlines : 1;
+// Room for n_cond conditions: parameter staging, per-condition statistics,
+// the condition order.
+static helk_status ensure_conds(helk_ctx *c, int n_cond) {
+  if (n_cond <= c->cond_cap) return HELK_OK;
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "conditions"));
+  if (c->cond_dev) cudaFree(c->cond_dev);
+  if (c->cstats) cudaFree(c->cstats);
+  if (c->cond_order) cudaFree(c->cond_order);
+  if (c->cond_host) cudaFreeHost(c->cond_host);
+  if (c->cstats_host) cudaFreeHost(c->cstats_host);
+  c->cond_dev = nullptr;
+  c->cstats = nullptr;
+  c->cond_order = nullptr;
+  c->cond_host = nullptr;
+  c->cstats_host = nullptr;
+  c->cond_cap = 0;
+  const int cap = std::max(n_cond, 8);
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->cond_dev, cap * sizeof(CondArgs)), "conditions"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->cstats, cap * sizeof(CondStats)), "conditions"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->cond_order, cap * sizeof(int)), "conditions"));
+  HELK_TRY(cuda_check(c, cudaMallocHost((void **)&c->cond_host, cap * sizeof(CondArgs)), "conditions"));
+  HELK_TRY(cuda_check(c, cudaMallocHost((void **)&c->cstats_host, cap * sizeof(CondStats)), "conditions"));
+  c->cond_cap = cap;
+  return HELK_OK;
+}
+
+// Buffers for n_cond conditions of the current line list and tile shape.
+static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts &o, int64_t ntiles) {
+  const int64_t nl = std::max<int64_t>(c->nlines, 1) * n_cond;
+  HELK_TRY(ensure_conds(c, n_cond));
   HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
-  HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, nl * 8, "line keys"));
-  const bool f32 = o.precision == HELK_PREC_F32_KAHAN;
-  if (f32)
+  HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, std::max<int64_t>(c->nlines, 1) * 8, "line keys"));
+  if (o.precision == HELK_PREC_F32_KAHAN)
     HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
                         "FP32 line records"));
-  // reset per-call statistics (keep error flags)
-  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->stats, 0, offsetof(DevStats, err_flags), c->stream), "stats"));
-  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->wmax, 0xFF, sizeof(long long), c->stream), "stats"));
+  HELK_TRY(ensure_tiles(c, ntiles * n_cond));
+  return HELK_OK;
+}
+
+// Statistics reset and line preparation (and the FP32 records) of n_cond
+// conditions: single != NULL passes the one condition by value, otherwise
+// they are read from c->cond_dev.
+static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single, double mass,
+                                 const helk_cutoff *cut, const helk_grid *g, const helk_opts &o) {
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->cstats, 0, n_cond * sizeof(CondStats), c->stream), "stats"));
+  for (int k = 0; k < n_cond; ++k)
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->cstats[k].wmax, 0xFF, sizeof(long long), c->stream), "stats"));
   if (c->nlines > 0) {
-    HELK_TRY(cuda_check(c, launch_lineprep(c, T, P, mass, o.q_ratio, *cut, *g, o.precision), "lineprep"));
-    if (f32) HELK_TRY(cuda_check(c, launch_pack32(c, *g), "pack32"));
+    HELK_TRY(cuda_check(c, launch_lineprep(c, n_cond, single, mass, *cut, *g), "lineprep"));
+    if (o.precision == HELK_PREC_F32_KAHAN) HELK_TRY(cuda_check(c, launch_pack32(c, n_cond, *g), "pack32"));
   }
+  return HELK_OK;
+}
+
+// Tile map, condition order and the persistent Voigt kernel.
+static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const helk_opts &o, double *kappa,
+                             int tile, int64_t ntiles) {
+  HELK_TRY(cuda_check(c, launch_tilemap(c, n_cond, *g, tile, ntiles), "tilemap"));
+  HELK_TRY(cuda_check(c, launch_cond_order(c, n_cond), "condition order"));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->tile_counter, 0, sizeof(unsigned int), c->stream),
+                      "voigt"));
+  HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
   return HELK_OK;
 }
 
@@ -306,21 +361,20 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   }
   const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
   const int64_t ntiles = (g->n + tile - 1) / tile;
-  HELK_TRY(ensure_tiles(c, ntiles));
+  HELK_TRY(ensure_call_buffers(c, 1, o, ntiles));
+  const CondArgs one{T, P, o.q_ratio, 0.0};
   stage_begin(c, HELK_STAGE_LINEPREP);
-  HELK_TRY(prepare_lines(c, T, P, mass, cut, g, o));
+  HELK_TRY(prepare_lines(c, 1, &one, mass, cut, g, o));
+  stage_end(c, HELK_STAGE_LINEPREP);
   if (c->nlines > 0) {
-    HELK_TRY(cuda_check(c, launch_tilemap(c, *g, tile, ntiles), "tilemap"));
-    stage_end(c, HELK_STAGE_LINEPREP);
     stage_begin(c, HELK_STAGE_VOIGT);
-    HELK_TRY(cuda_check(c, launch_voigt(c, *g, o, kappa, tile, ntiles), "voigt"));
+    HELK_TRY(run_voigt(c, 1, g, o, kappa, tile, ntiles));
     stage_end(c, HELK_STAGE_VOIGT);
-  } else {
-    stage_end(c, HELK_STAGE_LINEPREP);
-    if (!o.accumulate)
-      HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
+  } else if (!o.accumulate) {
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
   }
   c->last_n = g->n;
+  c->last_ncond = 1;
   c->have_opacity = (kappa == c->kappa);
   c->last_counted_regions = o.count_regions != 0;
   return HELK_OK;
@@ -343,8 +397,9 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   const int ncand = voigt_tile_candidates(o.precision, cand, 8);
   int64_t max_tiles = 0;
   for (int i = 0; i < ncand; ++i) max_tiles = std::max(max_tiles, (g->n + cand[i] - 1) / cand[i]);
-  HELK_TRY(ensure_tiles(c, max_tiles));
-  HELK_TRY(prepare_lines(c, T, P, mass, cut, g, o));
+  HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles));
+  const CondArgs one{T, P, o.q_ratio, 0.0};
+  HELK_TRY(prepare_lines(c, 1, &one, mass, cut, g, o));
   cudaEvent_t e0, e1;
   HELK_TRY(cuda_check(c, cudaEventCreate(&e0), "autotune"));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -356,19 +411,16 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   helk_status st = HELK_OK;
   for (int i = 0; i < ncand && st == HELK_OK; ++i) {
     const int64_t ntiles = (g->n + cand[i] - 1) / cand[i];
-    st = cuda_check(c, launch_tilemap(c, *g, cand[i], ntiles), "autotune");
-    if (st == HELK_OK) st = cuda_check(c, launch_voigt(c, *g, o, c->kappa, cand[i], ntiles), "autotune");
-    float ms = 0.f, tot = 0.f;
+    st = run_voigt(c, 1, g, o, c->kappa, cand[i], ntiles);  // warm-up
+    float ms = 0.f;
     const int reps = 3;
     if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e0, c->stream), "autotune");
-    for (int r = 0; r < reps && st == HELK_OK; ++r)
-      st = cuda_check(c, launch_voigt(c, *g, o, c->kappa, cand[i], ntiles), "autotune");
+    for (int r = 0; r < reps && st == HELK_OK; ++r) st = run_voigt(c, 1, g, o, c->kappa, cand[i], ntiles);
     if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e1, c->stream), "autotune");
     if (st == HELK_OK) st = cuda_check(c, cudaEventSynchronize(e1), "autotune");
     if (st == HELK_OK) st = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "autotune");
-    tot = ms / reps;
-    if (st == HELK_OK && tot < best_ms) {
-      best_ms = tot;
+    if (st == HELK_OK && ms / reps < best_ms) {
+      best_ms = ms / reps;
       best = cand[i];
     }
   }
@@ -383,16 +435,121 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   return HELK_OK;
 }
 
-helk_status helk_opacity_stats(helk_ctx *c, int64_t *n_evals, int64_t *region_counts) {
+// ---------------------------------------------------------------- batch --
+// Many (T, P) conditions in one persistent Voigt launch; the whole sequence
+// (condition upload from pinned staging, statistics reset, line preparation,
+// FP32 records, tile maps, condition order, Voigt kernel) is captured once
+// into a CUDA graph per call shape and replayed.
+static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const helk_cutoff *cut,
+                             const helk_grid *g, const helk_opts &o, const double *kappa, int tile) {
+  char b[512];
+  snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%p|%d|%p|%p|%p|%p", n_cond,
+           (long long)c->nlines, (const void *)c->nu0, mass, cut->kind, cut->value, cut->cap, g->nu_min,
+           g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions,
+           (const void *)kappa, tile, (const void *)c->rec64, (const void *)c->rec32,
+           (const void *)c->tile_lo, (const void *)c->cstats);
+  return std::string(b);
+}
+
+helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, const double *P,
+                               const double *q_ratio, double mass, const helk_cutoff *cut,
+                               const helk_grid *g, const helk_opts *opts, double *kappa_out) {
   if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_cond < 1 || !T || !P) return set_err(c, HELK_ERR_INVALID_ARG, "opacity_batch: need n_cond >= 1, T, P");
+  const helk_opts o = opts ? *opts : default_opts();
+  for (int k = 0; k < n_cond; ++k) {
+    helk_opts ok = o;
+    if (q_ratio) ok.q_ratio = q_ratio[k];
+    HELK_TRY(check_condition(c, T[k], P[k], mass, cut, g, ok));
+  }
+  if ((int64_t)n_cond * g->n > ((int64_t)1 << 40))
+    return set_err(c, HELK_ERR_INVALID_ARG, "opacity_batch: n_cond * grid size too large");
+  if (!c->nu0) return set_err(c, HELK_ERR_STATE, "opacity_batch: no line list uploaded");
+  HELK_TRY(bind_device(c));
+  double *kappa = kappa_out;
+  if (!kappa) {
+    HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, (int64_t)n_cond * g->n * 8, "opacity buffer"));
+    kappa = c->kappa;
+  }
+  if (c->nlines <= 0) {
+    if (!o.accumulate)
+      HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)n_cond * g->n * 8, c->stream), "opacity"));
+    c->last_n = g->n * n_cond;
+    c->last_ncond = n_cond;
+    c->have_opacity = (kappa == c->kappa);
+    return HELK_OK;
+  }
+  const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
+  const int64_t ntiles = (g->n + tile - 1) / tile;
+  HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles));
+  if (!c->cap_stream)
+    HELK_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "graph stream"));
+  if (!c->cond_ev) HELK_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->cond_ev, cudaEventDisableTiming), "graph"));
+  // the previous batch must have read the staging buffer before it changes
+  HELK_TRY(cuda_check(c, cudaEventSynchronize(c->cond_ev), "opacity_batch"));
+  for (int k = 0; k < n_cond; ++k) c->cond_host[k] = CondArgs{T[k], P[k], q_ratio ? q_ratio[k] : o.q_ratio, 0.0};
+  const std::string key = batch_key(c, n_cond, mass, cut, g, o, kappa, tile);
+  if (!c->gexec || c->gkey != key) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    helk_status st = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal),
+                                "graph capture");
+    if (st == HELK_OK) {
+      st = cuda_check(c, cudaMemcpyAsync(c->cond_dev, c->cond_host, n_cond * sizeof(CondArgs),
+                                         cudaMemcpyHostToDevice, c->stream),
+                      "graph capture");
+      if (st == HELK_OK) st = prepare_lines(c, n_cond, nullptr, mass, cut, g, o);
+      if (st == HELK_OK) st = run_voigt(c, n_cond, g, o, kappa, tile, ntiles);
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (st == HELK_OK) st = cuda_check(c, e, "graph capture");
+    }
+    c->stream = user;
+    if (st == HELK_OK) st = cuda_check(c, cudaGraphInstantiate(&c->gexec, graph, 0), "graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    if (st != HELK_OK) {
+      cudaGetLastError();
+      c->gexec = nullptr;
+      return st;
+    }
+    c->gkey = key;
+  }
+  stage_begin(c, HELK_STAGE_VOIGT);
+  HELK_TRY(cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"));
+  stage_end(c, HELK_STAGE_VOIGT);
+  HELK_TRY(cuda_check(c, cudaEventRecord(c->cond_ev, c->stream), "opacity_batch"));
+  c->last_n = g->n * n_cond;
+  c->last_ncond = n_cond;
+  c->have_opacity = (kappa == c->kappa);
+  c->last_counted_regions = o.count_regions != 0;
+  return HELK_OK;
+}
+
+helk_status helk_opacity_batch_stats(helk_ctx *c, int32_t n_cond, int64_t *n_evals, int64_t *region_counts) {
+  if (!c || n_cond < 1) return HELK_ERR_INVALID_ARG;
+  if (n_cond > c->last_ncond) return set_err(c, HELK_ERR_STATE, "batch_stats: more conditions than the last call");
   HELK_TRY(helk_sync(c));
-  if (n_evals) *n_evals = (int64_t)c->stats_host->evals;
-  if (region_counts) {
-    if (!c->last_counted_regions)
-      return set_err(c, HELK_ERR_STATE, "opacity_stats: last opacity ran without count_regions");
-    for (int r = 0; r < 4; ++r) region_counts[r] = (int64_t)c->stats_host->region[r];
+  HELK_TRY(cuda_check(c, cudaMemcpy(c->cstats_host, c->cstats, n_cond * sizeof(CondStats), cudaMemcpyDeviceToHost),
+                      "batch_stats"));
+  if (region_counts && !c->last_counted_regions)
+    return set_err(c, HELK_ERR_STATE, "batch_stats: last call ran without count_regions");
+  for (int k = 0; k < n_cond; ++k) {
+    if (n_evals) n_evals[k] = (int64_t)c->cstats_host[k].evals;
+    if (region_counts)
+      for (int r = 0; r < 4; ++r) region_counts[4 * k + r] = (int64_t)c->cstats_host[k].region[r];
   }
   return HELK_OK;
+}
+
+helk_status helk_opacity_stats(helk_ctx *c, int64_t *n_evals, int64_t *region_counts) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  if (c->last_ncond < 1) return set_err(c, HELK_ERR_STATE, "opacity_stats: no opacity computed yet");
+  return helk_opacity_batch_stats(c, 1, n_evals, region_counts);
 }
 
 helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbins, int32_t ncheb,
@@ -455,6 +612,28 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
                           "kdist copy"));
     HELK_TRY(helk_sync(c));
   }
+  return HELK_OK;
+}
+
+helk_status helk_transmission(helk_ctx *c, int32_t nbins, int64_t nb, const double *sorted,
+                              const double *coeffs, int32_t ncheb, int32_t ng, int32_t nm,
+                              const double *m, double *direct, double *fit) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (nbins < 1 || nm < 1 || !m) return set_err(c, HELK_ERR_INVALID_ARG, "transmission: nbins, nm >= 1 and m required");
+  if (sorted && (nb < 1 || !direct)) return set_err(c, HELK_ERR_INVALID_ARG, "transmission: nb >= 1 and direct required");
+  if (coeffs && (ncheb < 1 || ncheb > 32 || ng < 1 || ng > 16384 || !fit))
+    return set_err(c, HELK_ERR_INVALID_ARG, "transmission: 1 <= ncheb <= 32, 1 <= ng <= 16384 and fit required");
+  if (!sorted && !coeffs) return set_err(c, HELK_ERR_INVALID_ARG, "transmission: nothing to do");
+  for (int i = 0; i < nm; ++i)
+    if (!(is_fin(m[i]) && m[i] >= 0.0)) return set_err(c, HELK_ERR_INVALID_ARG, "transmission: m must be finite, >= 0");
+  HELK_TRY(bind_device(c));
+  HELK_TRY(ensure_buf(c, (void **)&c->mass_col, &c->mass_col_cap, (int64_t)nm * 8, "transmission"));
+  HELK_TRY(cuda_check(c, cudaMemcpyAsync(c->mass_col, m, (size_t)nm * 8, cudaMemcpyHostToDevice, c->stream),
+                      "transmission"));
+  HELK_TRY(cuda_check(c, launch_transmission(c, nbins, nb, sorted, coeffs, ncheb, ng, nm, c->mass_col, direct, fit),
+                      "transmission"));
+  // m is pageable host memory: the copy above has completed when it returned
   return HELK_OK;
 }
 

@@ -69,19 +69,28 @@ struct __align__(16) LineRec32 {
 };
 static_assert(sizeof(LineRec32) == 48, "LineRec32 must be 48 bytes");
 
-// Device-side statistics and error flags of the last call.
+// Device-side error flags and upload checks.
 struct DevStats {
-  unsigned long long evals;         // sum of window sizes
-  unsigned long long region[4];     // evaluations per method (optional):
-                                    // [916, GH3, GH1, 916 series terms]
-  long long wmax;                   // max half-width of a window in points
-  unsigned long long spmax_bits;    // max S' (non-negative double bits)
   int err_flags;                    // ERRF_*
   int bad_lines;                    // validation failures at upload
   int unsorted;                     // upload: nu0 not ordered
+  unsigned int tile_counter;        // next (condition, tile) item of the persistent Voigt kernel
+};
+
+// One (T, P) condition of a call.
+struct CondArgs {
+  double T, P, q_ratio, pad;
+};
+
+// Per-condition results of line preparation and of the Voigt kernel.
+struct CondStats {
+  unsigned long long evals;         // sum of window sizes
+  unsigned long long region[4];     // evaluations per method (optional):
+                                    // [916, GH3, GH1, 916 series terms]
+  long long wmax;                   // max half-width of a window in points (-1: none)
+  unsigned long long spmax_bits;    // max S' (non-negative double bits)
   int scale_exp;                    // FP32 form: strengths scaled by 2^-scale_exp
-  unsigned int tile_counter;        // reserved for dynamic tile scheduling
-  int pad2;
+  int pad;
 };
 enum { ERRF_TIMEOUT = 1 };
 
@@ -112,6 +121,17 @@ struct helk_ctx {
   int64_t tile_cap = 0;
   helk::DevStats *stats = nullptr;      // device
   helk::DevStats *stats_host = nullptr; // pinned
+  // conditions of the current call
+  helk::CondArgs *cond_dev = nullptr, *cond_host = nullptr;  // host side pinned
+  helk::CondStats *cstats = nullptr, *cstats_host = nullptr; // host side pinned
+  int *cond_order = nullptr;
+  int cond_cap = 0;
+  int last_ncond = 0;
+  cudaEvent_t cond_ev = nullptr;   // completion of the last batch that read cond_host
+  // CUDA graph of the batched path
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
   // opacity output owned by the context
   double *kappa = nullptr;
   int64_t kappa_cap = 0;
@@ -126,6 +146,9 @@ struct helk_ctx {
   int pinv_ncheb = 0;
   double *coef_dev = nullptr, *mean_dev = nullptr;
   int64_t coef_cap = 0, mean_cap = 0;
+  // column masses of helk_transmission
+  double *mass_col = nullptr;
+  int64_t mass_col_cap = 0;
   // generic upload scratch
   void *tmp = nullptr;
   int64_t tmp_cap = 0;
@@ -200,10 +223,15 @@ __device__ __forceinline__ void tma_load_1d(uint32_t dst_smem, const void *src, 
 // k_lines.cu
 cudaError_t launch_validate_lines(helk_ctx *c, int64_t n);
 cudaError_t launch_sort_lines(helk_ctx *c, int64_t n);  // orders SoA by nu0
-cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double q_ratio,
-                            const helk_cutoff &cut, const helk_grid &g, int precision);
-cudaError_t launch_pack32(helk_ctx *c, const helk_grid &g);
-cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t ntiles);
+// n_cond conditions: from c->cond_dev, or (n_cond == 1 and single != NULL)
+// the one condition passed by value.  Records of condition k start at
+// k * nlines; tile maps at k * ntiles.
+cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, double mass,
+                            const helk_cutoff &cut, const helk_grid &g);
+cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g);
+cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile, int64_t ntiles);
+// Conditions ordered by decreasing evaluation count (largest work first).
+cudaError_t launch_cond_order(helk_ctx *c, int n_cond);
 // k_voigt.cu
 // Tile length (points per CTA) for a grid of n points: a multiple of the
 // kernel's block size chosen so that the tiles fill whole waves of resident
@@ -211,12 +239,18 @@ cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t nt
 int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n);
 // Tile lengths the autotuner times (points per CTA).
 int voigt_tile_candidates(int precision, int *out, int max);
-cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, double *kappa,
-                         int tile_len, int64_t ntiles);
+// Persistent Voigt kernel over n_cond x ntiles (condition, tile) items taken
+// from DevStats::tile_counter (reset to 0 before the launch); kappa of
+// condition k at kappa + k * g.n.
+cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
+                         double *kappa, int tile_len, int64_t ntiles);
 // k_kdist.cu
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
                               double kappa_floor, double *coef, double *mean, double *kg_out);
 int64_t kdist_smem_max_points(helk_ctx *c);
+cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double *sorted,
+                                const double *coef, int ncheb, int ng, int nm, const double *m_dev,
+                                double *direct, double *fit);
 
 }  // namespace helk

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "helk_internal.cuh"
@@ -29,6 +30,33 @@ __device__ __forceinline__ uint32_t lanemask_lt_kd() {
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+// ------------------------------------------------------------- logarithm --
+// ln x for a positive normal double by the table-driven method of Tang
+// (ACM TOMS 16(4), 1990): x = 2^e m with m in [1, 2), c_j = 1 + j/128 where j
+// is the top 7 fraction bits of m, so f = m - c_j is exact and
+// r = f / c_j lies in [0, 1/128); then ln x = e ln2 + ln c_j + log1p(r) with
+// the Taylor series of log1p to r^7 (truncation < 2^-59 relative to r).  The
+// 128 entries ln c_j, 1/c_j live in shared memory.  Subnormal arguments take
+// the library log.
+constexpr double LOG_LN2 = 0.69314718055994530941723;
+
+__device__ __forceinline__ double log_table(double x, const double *lnc, const double *invc) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return log(x);
+  const int j = (int)((b >> 45) & 0x7F);
+  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const double cj = __longlong_as_double(0x3FF0000000000000LL | ((long long)j << 45));
+  const double r = (m - cj) * invc[j];
+  double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+  p = fma(p, r, 1.0 / 5.0);
+  p = fma(p, r, -1.0 / 4.0);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  p = fma(p, r * r, r);
+  return fma((double)(ex - 1023), LOG_LN2, lnc[j] + p);
 }
 
 // ------------------------------------------------------ pseudo-inverse --
@@ -220,6 +248,7 @@ __global__ void __launch_bounds__(KD_THREADS)
   __shared__ uint32_t wtot[32];
   __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
   __shared__ double red[KD_WARPS][NCHEB_MAX + 1];
+  __shared__ double s_lnc[128], s_invc[128];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t off = (int64_t)blockIdx.x * nb;
   unsigned long long *A, *B;
@@ -254,6 +283,12 @@ __global__ void __launch_bounds__(KD_THREADS)
   }
   const unsigned long long *S = cta_radix_sort(A, B, nb, hist, wtot, vand ^ vor);
   // sorted values out, c = P L and the bin sum
+  if (tid < 128) {
+    const double cj = 1.0 + tid / 128.0;
+    s_lnc[tid] = log(cj);
+    s_invc[tid] = 1.0 / cj;
+  }
+  __syncthreads();
   double b[NCHEB_MAX];
 #pragma unroll
   for (int k = 0; k < NCHEB_MAX; ++k) b[k] = 0.0;
@@ -262,7 +297,7 @@ __global__ void __launch_bounds__(KD_THREADS)
     const double kv = __longlong_as_double((long long)S[j]);
     if (kg_out) kg_out[off + j] = kv;
     ksum += kv;
-    const double L = log(kv > kappa_floor ? kv : kappa_floor);
+    const double L = log_table(kv > kappa_floor ? kv : kappa_floor, s_lnc, s_invc);
 #pragma unroll
     for (int k = 0; k < NCHEB_MAX; ++k)
       if (k < ncheb) b[k] += pinv[(int64_t)k * nb + j] * L;
@@ -313,6 +348,84 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
         kappa, nb, ncheb, kappa_floor, c->pinv, c->sort_a, c->sort_b, coef, mean, kg_out);
   }
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- transmission --
+// T_b(m) = int_0^1 exp(-k(g) m) dg per bin b and column mass m (Sec. 2.1):
+// from the sorted values by the midpoint rule on g_j = (j + 1/2)/N_b, and
+// from the Chebyshev fit by the midpoint rule on ng points.  One CTA per
+// (bin, block of column masses); FP64.
+constexpr int TR_THREADS = 256;
+
+__global__ void __launch_bounds__(TR_THREADS)
+    k_trans_direct(const double *__restrict__ sorted, int64_t nb, int nm, const double *__restrict__ m,
+                   double *__restrict__ out) {
+  __shared__ double red[TR_THREADS / 32];
+  const int b = blockIdx.x;
+  const double *k = sorted + (int64_t)b * nb;
+  for (int i = blockIdx.y; i < nm; i += gridDim.y) {
+    const double mi = m[i];
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < nb; j += TR_THREADS) s += exp(-k[j] * mi);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < TR_THREADS / 32; ++w) t += red[w];
+      out[(int64_t)b * nm + i] = t / (double)nb;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(TR_THREADS)
+    k_trans_fit(const double *__restrict__ coef, int ncheb, int ng, int nm, const double *__restrict__ m,
+                double *__restrict__ out) {
+  extern __shared__ double kfit[];  // ng values
+  const int b = blockIdx.x;
+  const double *c = coef + (int64_t)b * ncheb;
+  for (int j = threadIdx.x; j < ng; j += TR_THREADS) {
+    const double t = 2.0 * (((double)j + 0.5) / (double)ng) - 1.0;
+    double tkm1 = 1.0, tk = t, v = c[0];
+    if (ncheb > 1) v += c[1] * t;
+    for (int q = 2; q < ncheb; ++q) {
+      const double tn = 2.0 * t * tk - tkm1;
+      v += c[q] * tn;
+      tkm1 = tk;
+      tk = tn;
+    }
+    kfit[j] = exp(v);
+  }
+  __syncthreads();
+  for (int i = blockIdx.y * TR_THREADS + threadIdx.x; i < nm; i += gridDim.y * TR_THREADS) {
+    const double mi = m[i];
+    double s = 0.0;
+    for (int j = 0; j < ng; ++j) s += exp(-kfit[j] * mi);
+    out[(int64_t)b * nm + i] = s / (double)ng;
+  }
+}
+
+cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double *sorted,
+                                const double *coef, int ncheb, int ng, int nm, const double *m_dev,
+                                double *direct, double *fit) {
+  if (sorted && direct) {
+    dim3 grid(nbins, std::min(nm, 64));
+    k_trans_direct<<<grid, TR_THREADS, 0, c->stream>>>(sorted, nb, nm, m_dev, direct);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (coef && fit) {
+    const size_t smem = (size_t)ng * 8;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_trans_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid(nbins, (nm + TR_THREADS - 1) / TR_THREADS);
+    k_trans_fit<<<grid, TR_THREADS, smem, c->stream>>>(coef, ncheb, ng, nm, m_dev, fit);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 // ------------------------------------------------ allocation-free variant --

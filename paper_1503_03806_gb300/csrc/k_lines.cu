@@ -9,6 +9,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "helk_internal.cuh"
 
 namespace helk {
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const unsigned long l
 
 // Exclusive scan of m counts in place, one block of 1024 threads.
 __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *counts, int64_t m) {
-  __shared__ uint32_t part[1024];
   __shared__ uint32_t wsum[32];
   int64_t per = (m + 1023) / 1024;
   int64_t s0 = threadIdx.x * per, s1 = s0 + per < m ? s0 + per : m;
@@ -117,7 +118,6 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *counts, int64_t m) {
   }
   __syncthreads();
   uint32_t excl = v - s + (w > 0 ? wsum[w - 1] : 0u);
-  part[threadIdx.x] = excl;
   for (int64_t i = s0; i < s1; ++i) {
     uint32_t t = counts[i];
     counts[i] = excl;
@@ -231,7 +231,7 @@ cudaError_t launch_sort_lines(helk_ctx *c, int64_t n) {
 
 // ------------------------------------------------------- line preparation --
 struct PrepArgs {
-  double T, P, mass, q_ratio;
+  double mass;
   int cut_kind;
   double cut_value, cut_cap;
   double nu_min, dnu;
@@ -241,20 +241,28 @@ struct PrepArgs {
 // Per line and condition, in the operation order of the definitions:
 //   nu0' = nu0 + delta P                                   (Sec. 2.3 shift)
 //   S    = S0 (Q0/Q) e^{-c2E/T + c2E/T0} (1-e^{-c2 nu0/T})/(1-e^{-c2 nu0/T0})
+//   S   *= abundance weight of the line's species          (Sec. 2.1)
 //   Gamma_L = (T0/T)^n (g_air (P - P/2) + g_self P/2)      (Sec. 2.3)
 //   Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c               (Sec. 2.4)
 //   a = sqrt(ln2) Gamma_L / Gamma_D, ku = sqrt(ln2)/Gamma_D,
 //   S' = S sqrt(ln2/pi) / Gamma_D, window from the cutoff   (Sec. 2.5)
+// blockIdx.y is the condition; records of condition k start at k * n.
 __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
                            const double *__restrict__ El, const double *__restrict__ gair,
                            const double *__restrict__ gself, const double *__restrict__ ncoll,
                            const double *__restrict__ delta, const double *__restrict__ lmass,
-                           const double *__restrict__ lweight, PrepArgs A, LineRec64 *__restrict__ rec,
-                           double *__restrict__ ckey, DevStats *st) {
+                           const double *__restrict__ lweight, PrepArgs A,
+                           const CondArgs *__restrict__ conds, CondArgs single,
+                           LineRec64 *__restrict__ rec_all, double *__restrict__ ckey,
+                           CondStats *cst_all) {
+  const int cond = blockIdx.y;
+  const CondArgs C = conds ? conds[cond] : single;
+  LineRec64 *rec = rec_all + (int64_t)cond * n;
+  CondStats *cst = cst_all + cond;
   unsigned long long evals = 0;
   long long wmax = -1;
   unsigned long long spmax = 0;
-  const double vth = sqrt(2.0 * LN2 * KB * A.T / (A.mass * AMU)) / CLIGHT;
+  const double vth = sqrt(2.0 * LN2 * KB * C.T / (A.mass * AMU)) / CLIGHT;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = nu0[l];
@@ -263,18 +271,18 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
     const double gs = gself ? gself[l] : ga;
     const double nc = ncoll ? ncoll[l] : 0.5;
     double S = S0[l];
-    const double nu0p = v0 + dl * A.P;
+    const double nu0p = v0 + dl * C.P;
     if (El) {
       const double E = El[l];
-      const double boltz = exp(-C2 * E / A.T + C2 * E / T0);
-      const double stim = v0 > 0.0 ? expm1(-C2 * v0 / A.T) / expm1(-C2 * v0 / T0) : T0 / A.T;
-      S = S * A.q_ratio * boltz * stim;
+      const double boltz = exp(-C2 * E / C.T + C2 * E / T0);
+      const double stim = v0 > 0.0 ? expm1(-C2 * v0 / C.T) / expm1(-C2 * v0 / T0) : T0 / C.T;
+      S = S * C.q_ratio * boltz * stim;
     }
     if (lweight) S = S * lweight[l];
-    const double tfac = (nc == 0.5) ? sqrt(T0 / A.T) : pow(T0 / A.T, nc);
-    const double pself = 0.5 * A.P;
-    const double gL = tfac * (ga * (A.P - pself) + gs * pself);
-    const double gD = nu0p * (lmass ? sqrt(2.0 * LN2 * KB * A.T / (lmass[l] * AMU)) / CLIGHT : vth);
+    const double tfac = (nc == 0.5) ? sqrt(T0 / C.T) : pow(T0 / C.T, nc);
+    const double pself = 0.5 * C.P;
+    const double gL = tfac * (ga * (C.P - pself) + gs * pself);
+    const double gD = nu0p * (lmass ? sqrt(2.0 * LN2 * KB * C.T / (lmass[l] * AMU)) / CLIGHT : vth);
     const double a = SQRTLN2 * gL / gD;
     const double ku = SQRTLN2 / gD;
     const double Sp = S * SQRTLN2PI / gD;
@@ -320,7 +328,7 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
     double ck = floor((v0 - A.nu_min) / A.dnu);
     if (ck < -4.0e15) ck = -4.0e15;
     if (ck > 4.0e15) ck = 4.0e15;
-    ckey[l] = ck;
+    if (cond == 0) ckey[l] = ck;
     if (r.ihi >= r.ilo) {
       evals += (unsigned long long)(r.ihi - r.ilo + 1);
       long long c0 = (long long)ck;
@@ -340,39 +348,49 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
     if (s2 > spmax) spmax = s2;
   }
   if ((threadIdx.x & 31) == 0) {
-    if (evals) atomicAdd(&st->evals, evals);
-    if (wmax >= 0) atomicMax(&st->wmax, wmax);
-    if (spmax) atomicMax(&st->spmax_bits, spmax);
+    if (evals) atomicAdd(&cst->evals, evals);
+    if (wmax >= 0) atomicMax(&cst->wmax, wmax);
+    if (spmax) atomicMax(&cst->spmax_bits, spmax);
   }
 }
 
-cudaError_t launch_lineprep(helk_ctx *c, double T, double P, double mass, double q_ratio,
-                            const helk_cutoff &cut, const helk_grid &g, int precision) {
-  (void)precision;
+static int line_blocks(helk_ctx *c, int64_t n, int n_cond) {
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)c->num_sms * 16 / std::max(1, n_cond));
+  if (blocks > cap) blocks = cap;
+  return (int)std::max<int64_t>(1, blocks);
+}
+
+cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, double mass,
+                            const helk_cutoff &cut, const helk_grid &g) {
   const int64_t n = c->nlines;
   if (n <= 0) return cudaSuccess;
-  PrepArgs A{T, P, mass, q_ratio, cut.kind, cut.value, cut.cap, g.nu_min, g.dnu, g.n};
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
-  k_lineprep<<<blocks, 256, 0, c->stream>>>(
+  PrepArgs A{mass, cut.kind, cut.value, cut.cap, g.nu_min, g.dnu, g.n};
+  const CondArgs one = single ? *single : CondArgs{0, 0, 0, 0};
+  dim3 grid(line_blocks(c, n, n_cond), n_cond);
+  k_lineprep<<<grid, 256, 0, c->stream>>>(
       n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair, c->has_gself ? c->gself : nullptr,
       c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr,
-      c->has_mass ? c->lmass : nullptr, c->has_weight ? c->lweight : nullptr, A, c->rec64, c->ckey,
-      c->stats);
+      c->has_mass ? c->lmass : nullptr, c->has_weight ? c->lweight : nullptr, A,
+      single ? nullptr : c->cond_dev, one, c->rec64, c->ckey, c->cstats);
   return cudaGetLastError();
 }
 
 // ----------------------------------------------------- FP32 line records --
 // From the FP64 records: strengths scaled by 2^-E (E from the largest S' of
-// the call, so every scaled term is <= 1 and the FP32 range covers 38
+// the condition, so every scaled term is <= 1 and the FP32 range covers 38
 // decades below it); the centre as the integer grid index c plus the FP32
 // offset phi = (nu0' - nu_c) ku, so that u_i = (i - c) beta - phi keeps full
 // relative precision near the line centre.
-__global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64, double nu_min, double dnu,
-                         DevStats *st, LineRec32 *__restrict__ r32) {
-  const double spmax = __longlong_as_double((long long)st->spmax_bits);
+__global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu,
+                         CondStats *cst_all, LineRec32 *__restrict__ r32_all) {
+  const int cond = blockIdx.y;
+  const LineRec64 *r64 = r64_all + (int64_t)cond * n;
+  LineRec32 *r32 = r32_all + (int64_t)cond * n;
+  CondStats *cst = cst_all + cond;
+  const double spmax = __longlong_as_double((long long)cst->spmax_bits);
   const int E = spmax > 0.0 ? ilogb(spmax) + 1 : 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->scale_exp = E;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cst->scale_exp = E;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const LineRec64 r = r64[l];
@@ -397,28 +415,29 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64, double nu
   }
 }
 
-cudaError_t launch_pack32(helk_ctx *c, const helk_grid &g) {
+cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   const int64_t n = c->nlines;
   if (n <= 0) return cudaSuccess;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
-  k_pack32<<<blocks, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->stats, c->rec32);
+  dim3 grid(line_blocks(c, n, n_cond), n_cond);
+  k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->cstats, c->rec32);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- tile map --
 // Lines overlapping grid tile [A, B) have their reference index in
-// [A - W, B - 1 + W], W = max half-width of any window: a contiguous range
-// of the nu0-ordered list, found by two binary searches.
+// [A - W, B - 1 + W], W = max half-width of any window of the condition: a
+// contiguous range of the nu0-ordered list, found by two binary searches.
 __global__ void k_tilemap(int64_t nlines, const double *__restrict__ ckey, int64_t ngrid, int tile,
-                          int64_t ntiles, const DevStats *__restrict__ st, int32_t *tlo,
+                          int64_t ntiles, const CondStats *__restrict__ cst, int32_t *tlo,
                           int32_t *thi) {
+  const int cond = blockIdx.y;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= ntiles) return;
-  long long W = st->wmax;
+  const int64_t o = (int64_t)cond * ntiles + t;
+  long long W = cst[cond].wmax;
   if (W < 0) {  // no line has a non-empty window
-    tlo[t] = 0;
-    thi[t] = 0;
+    tlo[o] = 0;
+    thi[o] = 0;
     return;
   }
   double A = (double)(t * tile);
@@ -435,14 +454,35 @@ __global__ void k_tilemap(int64_t nlines, const double *__restrict__ ckey, int64
     int64_t mid = (lo + hi) >> 1;
     if (ckey[mid] <= khi) lo = mid + 1; else hi = mid;
   }
-  tlo[t] = (int32_t)first;
-  thi[t] = (int32_t)lo;
+  tlo[o] = (int32_t)first;
+  thi[o] = (int32_t)lo;
 }
 
-cudaError_t launch_tilemap(helk_ctx *c, const helk_grid &g, int tile, int64_t ntiles) {
-  int blocks = (int)((ntiles + 127) / 128);
-  k_tilemap<<<blocks, 128, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->stats,
-                                           c->tile_lo, c->tile_hi);
+cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile, int64_t ntiles) {
+  dim3 grid((unsigned)((ntiles + 127) / 128), n_cond);
+  k_tilemap<<<grid, 128, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->cstats,
+                                         c->tile_lo, c->tile_hi);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- condition order --
+// Largest evaluation count first, so the persistent Voigt kernel's last
+// items are the cheapest (ties keep the input order).
+__global__ void k_cond_order(int n_cond, const CondStats *__restrict__ cst, int *order) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < n_cond; ++i) {
+    const unsigned long long e = cst[i].evals;
+    int j = i;
+    while (j > 0 && cst[order[j - 1]].evals < e) {
+      order[j] = order[j - 1];
+      --j;
+    }
+    order[j] = i;
+  }
+}
+
+cudaError_t launch_cond_order(helk_ctx *c, int n_cond) {
+  k_cond_order<<<1, 32, 0, c->stream>>>(n_cond, c->cstats, c->cond_order);
   return cudaGetLastError();
 }
 

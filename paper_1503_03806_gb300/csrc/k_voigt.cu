@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "helk_internal.cuh"
 
 namespace helk {
@@ -128,20 +130,22 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 // ------------------------------------------------------ line staging ----
-// Double-buffered bulk-copy pipeline over the line range [l0, l1).
+// Double-buffered bulk-copy pipeline over a line range [l0, l1).  The two
+// mbarriers are initialised once per CTA; chunks are numbered across all the
+// ranges a persistent CTA processes (gch), which fixes each chunk's buffer
+// (gch & 1) and barrier phase ((gch >> 1) & 1).
 template <typename Rec, int LCH>
 struct LineStager {
   Rec (*sl)[LCH];
   uint32_t mb[2];
   int l0, l1, nch;
+  uint32_t gbase;  // global number of this range's chunk 0
   const Rec *rec;
 
-  __device__ void init(Rec (*buf)[LCH], unsigned long long *mbar, const Rec *r, int a, int b) {
+  __device__ void init(Rec (*buf)[LCH], unsigned long long *mbar) {
     sl = buf;
-    rec = r;
-    l0 = a;
-    l1 = b;
-    nch = (l1 - l0 + LCH - 1) / LCH;
+    gbase = 0;
+    nch = 0;
     mb[0] = smem_addr(&mbar[0]);
     mb[1] = smem_addr(&mbar[1]);
     if (threadIdx.x == 0) {
@@ -150,38 +154,71 @@ struct LineStager {
       fence_mbar_init();
     }
     __syncthreads();
+  }
+  // Start a new range; every thread must have finished the previous one.
+  __device__ void begin(const Rec *r, int a, int b) {
+    gbase += nch;
+    rec = r;
+    l0 = a;
+    l1 = b;
+    nch = (l1 - l0 + LCH - 1) / LCH;
     if (threadIdx.x == 0 && nch > 0) issue(0);
   }
   __device__ int count(int ch) const { return min(LCH, l1 - l0 - ch * LCH); }
+  __device__ const Rec *buffer(int ch) const { return sl[(gbase + ch) & 1]; }
   __device__ void issue(int ch) {
-    tma_load_1d(smem_addr(&sl[ch & 1][0]), rec + l0 + ch * LCH, (uint32_t)(count(ch) * sizeof(Rec)),
-                mb[ch & 1]);
+    const uint32_t g = gbase + ch;
+    tma_load_1d(smem_addr(&sl[g & 1][0]), rec + l0 + ch * LCH, (uint32_t)(count(ch) * sizeof(Rec)),
+                mb[g & 1]);
   }
   // Prefetch chunk ch+1, wait for chunk ch.  Returns false (for every thread)
   // if the wait gave up; the caller must then return.
   __device__ bool acquire(int ch, int *flags) {
     if (threadIdx.x == 0 && ch + 1 < nch) issue(ch + 1);
-    const bool ok = mbar_wait_bounded(mb[ch & 1], (ch >> 1) & 1, flags, WAIT_LIMIT);
+    const uint32_t g = gbase + ch;
+    const bool ok = mbar_wait_bounded(mb[g & 1], (g >> 1) & 1, flags, WAIT_LIMIT);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0 && ch + 1 < nch)
-        mbar_wait_bounded(mb[(ch + 1) & 1], ((ch + 1) >> 1) & 1, flags, WAIT_LIMIT);
+        mbar_wait_bounded(mb[(g + 1) & 1], ((g + 1) >> 1) & 1, flags, WAIT_LIMIT);
       return false;
     }
     return true;
   }
 };
 
+// Next (condition, tile) item of a persistent CTA: -1 when none is left.
+__device__ __forceinline__ int next_item(DevStats *st, int nitems, int *s_item) {
+  if (threadIdx.x == 0) *s_item = (int)atomicAdd(&st->tile_counter, 1u);
+  __syncthreads();
+  const int item = *s_item;
+  __syncthreads();
+  return item < nitems ? item : -1;
+}
+
 // ------------------------------------------------------------ FP64 form --
+// Persistent: each CTA takes (condition, tile) items until none are left;
+// items of the condition with the most evaluations come first.
 template <int BLOCK, int PPT, int LCH, bool COUNT>
 __global__ void __launch_bounds__(BLOCK)
-    k_voigt_f64(const LineRec64 *__restrict__ rec, const int32_t *__restrict__ tlo,
-                const int32_t *__restrict__ thi, double nu_min, double dnu, int ngrid, int nslot,
-                double weight, int accumulate, double *__restrict__ kappa, DevStats *st) {
+    k_voigt_f64(const LineRec64 *__restrict__ rec_all, int64_t nlines,
+                const int32_t *__restrict__ tlo_all, const int32_t *__restrict__ thi_all,
+                int64_t ntiles, const int *__restrict__ cond_order, int n_cond, double nu_min,
+                double dnu, int ngrid, int nslot, double weight, int accumulate,
+                double *__restrict__ kappa_all, CondStats *cst, DevStats *st) {
   __shared__ __align__(128) LineRec64 sl[2][LCH];
   __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ int s_item;
   const int tid = threadIdx.x;
   const int tile_len = BLOCK * nslot;
-  const int base = blockIdx.x * tile_len;
+  LineStager<LineRec64, LCH> stg;
+  stg.init(sl, mbar);
+  const int nitems = (int)(ntiles * n_cond);
+  for (int item = next_item(st, nitems, &s_item); item >= 0; item = next_item(st, nitems, &s_item)) {
+  const int cond = cond_order[item / ntiles];
+  const int64_t tile = item % ntiles;
+  const LineRec64 *rec = rec_all + cond * nlines;
+  double *kappa = kappa_all + (int64_t)cond * ngrid;
+  const int base = (int)(tile * tile_len);
   double nu[PPT], acc[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
@@ -190,12 +227,11 @@ __global__ void __launch_bounds__(BLOCK)
     acc[k] = 0.0;
   }
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  LineStager<LineRec64, LCH> stg;
-  stg.init(sl, mbar, rec, tlo[blockIdx.x], thi[blockIdx.x]);
+  stg.begin(rec, tlo_all[cond * ntiles + tile], thi_all[cond * ntiles + tile]);
   for (int ch = 0; ch < stg.nch; ++ch) {
     if (!stg.acquire(ch, &st->err_flags)) return;
     const int cnum = stg.count(ch);
-    const LineRec64 *buf = sl[ch & 1];
+    const LineRec64 *buf = stg.buffer(ch);
     for (int j = 0; j < cnum; ++j) {
       const LineRec64 &L = buf[j];
       const int ilo = L.ilo, ihi = L.ihi;
@@ -249,8 +285,9 @@ __global__ void __launch_bounds__(BLOCK)
     for (int r = 0; r < 4; ++r) {
       unsigned long long v = cnt[r];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((tid & 31) == 0 && v) atomicAdd(&st->region[r], v);
+      if ((tid & 31) == 0 && v) atomicAdd(&cst[cond].region[r], v);
     }
+  }
   }
 }
 
@@ -264,8 +301,7 @@ __global__ void __launch_bounds__(BLOCK)
 // interleave); mixed pairs -- those containing a method boundary or the line
 // core -- decide per point.
 enum { CLS_GH1 = 0, CLS_GH3 = 1, CLS_MIXED = 2 };
-constexpr float F32_T1 = 1.2247448714f;     // GH3 node sqrt(3/2)
-constexpr float F32_T1SQ = 1.5f;            // its square
+constexpr float F32_T1SQ = 1.5f;            // square of the GH3 node sqrt(3/2)
 constexpr int KAHAN_GROUP = 8;              // lines per compensated partial
 
 // Hardware reciprocal approximation (max relative error ~1 ulp); every
@@ -296,9 +332,11 @@ __device__ __forceinline__ float gh3_term(float u, float r2, float P3h) {
 
 template <int BLOCK, int NSLOT, int LCH, bool COUNT>
 __global__ void __launch_bounds__(BLOCK)
-    k_voigt_f32(const LineRec32 *__restrict__ rec, const int32_t *__restrict__ tlo,
-                const int32_t *__restrict__ thi, int ngrid, double weight, int accumulate,
-                double *__restrict__ kappa, DevStats *st) {
+    k_voigt_f32(const LineRec32 *__restrict__ rec_all, int64_t nlines,
+                const int32_t *__restrict__ tlo_all, const int32_t *__restrict__ thi_all,
+                int64_t ntiles, const int *__restrict__ cond_order, int n_cond, int ngrid,
+                double weight, int accumulate, double *__restrict__ kappa_all, CondStats *cst,
+                DevStats *st) {
   // Warp w of the CTA owns the WSPAN consecutive points starting at
   // base + w WSPAN; lane l holds points base + w WSPAN + 32 k + l.  Method
   // classes are decided per (line, warp), so only the warps whose span holds
@@ -307,8 +345,17 @@ __global__ void __launch_bounds__(BLOCK)
   constexpr int WSPAN = 32 * NSLOT;
   __shared__ __align__(128) LineRec32 sl[2][LCH];
   __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ int s_item;
   const int lane = threadIdx.x & 31;
-  const int base = blockIdx.x * TILE;
+  LineStager<LineRec32, LCH> stg;
+  stg.init(sl, mbar);
+  const int nitems = (int)(ntiles * n_cond);
+  for (int item = next_item(st, nitems, &s_item); item >= 0; item = next_item(st, nitems, &s_item)) {
+  const int cond = cond_order[item / ntiles];
+  const int64_t tile = item % ntiles;
+  const LineRec32 *rec = rec_all + cond * nlines;
+  double *kappa = kappa_all + (int64_t)cond * ngrid;
+  const int base = (int)(tile * TILE);
   const int wbase = base + (threadIdx.x >> 5) * WSPAN;
   // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
   // into part[k] (relative error <= 7 u) and Kahan-adds the partial into
@@ -322,12 +369,11 @@ __global__ void __launch_bounds__(BLOCK)
   }
   int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  LineStager<LineRec32, LCH> stg;
-  stg.init(sl, mbar, rec, tlo[blockIdx.x], thi[blockIdx.x]);
+  stg.begin(rec, tlo_all[cond * ntiles + tile], thi_all[cond * ntiles + tile]);
   for (int ch = 0; ch < stg.nch; ++ch) {
     if (!stg.acquire(ch, &st->err_flags)) return;
     const int cnum = stg.count(ch);
-    const LineRec32 *buf = sl[ch & 1];
+    const LineRec32 *buf = stg.buffer(ch);
     for (int j = 0; j < cnum; ++j) {
       const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
       const int lo = max(ilo, wbase), hi = min(ihi, wbase + WSPAN - 1);
@@ -426,7 +472,7 @@ __global__ void __launch_bounds__(BLOCK)
     }
     __syncthreads();
   }
-  const double scale = ldexp(weight, st->scale_exp);
+  const double scale = ldexp(weight, cst[cond].scale_exp);
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) {
     kahan_add(sum[k], comp[k], part[k]);
@@ -440,8 +486,9 @@ __global__ void __launch_bounds__(BLOCK)
     for (int r = 0; r < 4; ++r) {
       unsigned long long v = cnt[r];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0 && v) atomicAdd(&st->region[r], v);
+      if (lane == 0 && v) atomicAdd(&cst[cond].region[r], v);
     }
+  }
   }
 }
 
@@ -529,34 +576,48 @@ int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n) {
   return F64_BLOCK * pick_nslot(n, F64_BLOCK, F64_PPT, slots);
 }
 
-cudaError_t launch_voigt(helk_ctx *c, const helk_grid &g, const helk_opts &o, double *kappa,
-                         int tile_len, int64_t ntiles) {
-  const unsigned grid = (unsigned)ntiles;
+template <typename K>
+static unsigned persistent_grid(helk_ctx *c, K kern, int block, int64_t nitems) {
+  const int64_t slots = resident_ctas(c, kern, block);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(slots, nitems));
+}
+
+cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
+                         double *kappa, int tile_len, int64_t ntiles) {
+  const int64_t nitems = ntiles * n_cond;
   if (o.precision == HELK_PREC_F32_KAHAN) {
     const int ns = tile_len / F32_BLOCK;
-#define X(NS)                                                                                     \
-    if (ns == NS) {                                                                               \
-      if (o.count_regions)                                                                        \
-        k_voigt_f32<F32_BLOCK, NS, F32_LCH, true><<<grid, F32_BLOCK, 0, c->stream>>>(             \
-            c->rec32, c->tile_lo, c->tile_hi, (int)g.n, o.weight, o.accumulate, kappa, c->stats); \
-      else                                                                                        \
-        k_voigt_f32<F32_BLOCK, NS, F32_LCH, false><<<grid, F32_BLOCK, 0, c->stream>>>(            \
-            c->rec32, c->tile_lo, c->tile_hi, (int)g.n, o.weight, o.accumulate, kappa, c->stats); \
-      return cudaGetLastError();                                                                  \
+#define X(NS)                                                                                   \
+    if (ns == NS) {                                                                             \
+      if (o.count_regions) {                                                                    \
+        auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, true>;                                   \
+        kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
+            c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
+            o.weight, o.accumulate, kappa, c->cstats, c->stats);                                 \
+      } else {                                                                                  \
+        auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false>;                                  \
+        kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
+            c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
+            o.weight, o.accumulate, kappa, c->cstats, c->stats);                                 \
+      }                                                                                         \
+      return cudaGetLastError();                                                                \
     }
     HELK_F32_NSLOTS(X)
 #undef X
     return cudaErrorInvalidValue;
   }
   const int nslot = tile_len / F64_BLOCK;
-  if (o.count_regions)
-    k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true><<<grid, F64_BLOCK, 0, c->stream>>>(
-        c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
-        kappa, c->stats);
-  else
-    k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false><<<grid, F64_BLOCK, 0, c->stream>>>(
-        c->rec64, c->tile_lo, c->tile_hi, g.nu_min, g.dnu, (int)g.n, nslot, o.weight, o.accumulate,
-        kappa, c->stats);
+  if (o.count_regions) {
+    auto kern = k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true>;
+    kern<<<persistent_grid(c, kern, F64_BLOCK, nitems), F64_BLOCK, 0, c->stream>>>(
+        c->rec64, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, g.nu_min, g.dnu,
+        (int)g.n, nslot, o.weight, o.accumulate, kappa, c->cstats, c->stats);
+  } else {
+    auto kern = k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false>;
+    kern<<<persistent_grid(c, kern, F64_BLOCK, nitems), F64_BLOCK, 0, c->stream>>>(
+        c->rec64, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, g.nu_min, g.dnu,
+        (int)g.n, nslot, o.weight, o.accumulate, kappa, c->cstats, c->stats);
+  }
   return cudaGetLastError();
 }
 

@@ -69,6 +69,10 @@ SIGNATURES = [
     ("helk_set_profiling", ctypes.c_int, [_P, _I32]),
     ("helk_stage_times", ctypes.c_int, [_P, _P, _P]),
     ("helk_kdist_static", ctypes.c_int, [_P, _I64, _I32, _I32, _D, _P, _P, _P, _P]),
+    ("helk_opacity_batch", ctypes.c_int, [_P, _I32, _P, _P, _P, _D, ctypes.POINTER(helk_cutoff),
+                                          ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts), _P]),
+    ("helk_opacity_batch_stats", ctypes.c_int, [_P, _I32, _P, _P]),
+    ("helk_transmission", ctypes.c_int, [_P, _I32, _I64, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     ("helk_autotune", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(helk_cutoff),
                                      ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
                                      ctypes.POINTER(_I32)]),
@@ -253,6 +257,50 @@ class Context:
                       int(bool(count_regions)))
         _check(self.h, helk_opacity(self.h, T, P, mass, _cut(cut), g, o, ctypes.c_void_p(out.data_ptr())))
         return out
+
+    def opacity_batch(self, T, P, mass, cut, grid, out=None, precision=HELK_PREC_F64, q_ratio=None,
+                      accumulate=False, weight=1.0, count_regions=False):
+        """n_cond conditions (T[k], P[k]) in one graph-captured persistent launch;
+        returns kappa as a (n_cond, n) float64 tensor."""
+        torch = self.torch
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        nc = T.shape[0]
+        q = None if q_ratio is None else np.ascontiguousarray(q_ratio, dtype=np.float64)
+        g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
+        if out is None:
+            out = torch.empty((nc, int(grid[2])), dtype=torch.float64, device=self.device)
+        assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous()
+        o = helk_opts(int(precision), int(bool(accumulate)), float(weight), 1.0, int(bool(count_regions)))
+        _check(self.h, lib.helk_opacity_batch(self.h, nc, T.ctypes.data_as(_P), P.ctypes.data_as(_P),
+                                              None if q is None else q.ctypes.data_as(_P), float(mass),
+                                              ctypes.byref(_cut(cut)), ctypes.byref(g), ctypes.byref(o),
+                                              ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def transmission(self, nbins, m, sorted_k=None, coeffs=None, ng=None):
+        """Per-bin transmission for column masses m: (direct, fit), each a
+        (nbins, nm) tensor or None."""
+        torch = self.torch
+        m = np.ascontiguousarray(np.atleast_1d(m), dtype=np.float64)
+        nm = m.shape[0]
+        nb = 0 if sorted_k is None else sorted_k.numel() // nbins
+        ncheb = 0 if coeffs is None else coeffs.shape[-1]
+        if ng is None:
+            ng = max(nb, 1)
+        direct = None if sorted_k is None else torch.empty((nbins, nm), dtype=torch.float64, device=self.device)
+        fit = None if coeffs is None else torch.empty((nbins, nm), dtype=torch.float64, device=self.device)
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        _check(self.h, lib.helk_transmission(self.h, int(nbins), int(nb), p(sorted_k), p(coeffs), int(ncheb),
+                                             int(ng), int(nm), m.ctypes.data_as(_P), p(direct), p(fit)))
+        return direct, fit
+
+    def batch_stats(self, n_cond, with_regions=False):
+        ev = np.zeros(n_cond, dtype=np.int64)
+        reg = np.zeros((n_cond, 4), dtype=np.int64)
+        _check(self.h, lib.helk_opacity_batch_stats(self.h, int(n_cond), ev.ctypes.data_as(_P),
+                                                    reg.ctypes.data_as(_P) if with_regions else None))
+        return ev, (reg if with_regions else None)
 
     def autotune(self, T, P, mass, cut, grid, precision=HELK_PREC_F64, q_ratio=1.0):
         """Time the built Voigt tile shapes on this condition; keep the
