@@ -108,6 +108,12 @@ typedef struct {
     double q_ratio;     /* Q(T0)/Q(T), used only when E_lower was uploaded   */
     int32_t count_regions; /* 1: also count evaluations per method (slower;
                               read with helk_opacity_stats)                   */
+    int32_t surrogate;  /* FP32 form only: 1 routes Algorithm-916 evaluations
+                           that fall in the surrogate network's validated
+                           cells to the network (helk_surrogate_*); error
+                           <= 1e-4 relative per routed term.  The routed
+                           terms are added with atomics, so results are no
+                           longer bitwise reproducible.                    */
 } helk_opts;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream`
@@ -225,6 +231,58 @@ enum { HELK_STAGE_LINEPREP = 0, HELK_STAGE_VOIGT = 1, HELK_STAGE_KDIST = 2,
        HELK_STAGE_SETUP = 3, HELK_NSTAGES = 4 };
 helk_status helk_set_profiling(helk_ctx *ctx, int32_t on);
 helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
+
+/* ----------------------------------------------------------------------
+ * Surrogate network for the Voigt function (an addition to the paper's
+ * method: a 2 -> 64 -> 64 -> 64 -> 1 SiLU network, BF16 tensor-core MMAs with
+ * FP32 accumulation, that stands in for Algorithm 916 (Sec. 2.5, the region
+ * a^2 + u^2 < 100) as K(x, y) = K_ref(x, y) exp(net(f1, f2)),
+ *   K_ref = e^{-x^2} erfcx(y) + (1 - e^{-x^2}) y / (sqrt(pi)(x^2 + y^2)),
+ *   f1 = 2 asinh|x| / asinh(10) - 1,  f2 = 2 (log10 y + 4) / 5 - 1,
+ * for 1e-4 <= y < 10.  Parameters: 8577 floats, W1[2][64], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4 (W[in][out]).
+ * Training targets are this library's FP64 Algorithm 916; the same judges
+ * the network cell by cell (helk_surrogate_validate), and only validated
+ * cells are routed to it (helk_opts.surrogate).
+ * ------------------------------------------------------------------- */
+/* (Re)initialise the network with seeded normal weights, zero biases. */
+helk_status helk_surrogate_init(helk_ctx *ctx, uint64_t seed);
+/* Copy the parameters to get_host (8577 floats) and/or replace them from
+ * set_host (resets the optimiser state); either may be NULL.  Synchronises. */
+helk_status helk_surrogate_params(helk_ctx *ctx, float *get_host,
+                                  const float *set_host);
+/* n seeded samples of the core region (|x| asinh-uniform in [0, 10], y
+ * log-uniform in [1e-4, 10), x^2 + y^2 < 100): features feat[2i], feat[2i+1],
+ * target ln(K/K_ref) with K by FP64 Algorithm 916, and optionally x, y.
+ * Device pointers. */
+helk_status helk_surrogate_samples(helk_ctx *ctx, int64_t n, uint64_t seed,
+                                   float *feat, float *target, double *x,
+                                   double *y);
+/* Gradient of the mean squared residual error over n samples (device
+ * feat/target) at the current parameters, to grad_host (8577 floats) and
+ * the loss to loss_host; no update.  Synchronises. */
+helk_status helk_surrogate_grad(helk_ctx *ctx, int64_t n, const float *feat,
+                                const float *target, float *grad_host,
+                                double *loss_host);
+/* Train with Adam on n_samples fresh samples (seed) for `epochs` passes in
+ * minibatches of `batch` (>= 128), learning rate lr with cosine decay to 1 %.
+ * final_loss (host, optional): mean squared residual error of the last
+ * epoch.  Synchronises after every epoch. */
+helk_status helk_surrogate_train(helk_ctx *ctx, int64_t n_samples,
+                                 uint64_t seed, int32_t epochs, int32_t batch,
+                                 double lr, double *final_loss);
+/* K(x_i, y_i) by the network for n points (device arrays). */
+helk_status helk_surrogate_eval(helk_ctx *ctx, int64_t n, const double *x,
+                                const double *y, double *k);
+/* Held-out check on an nx x ny partition of the feature square with
+ * per_cell^2 points at sub-cell centres (points with x^2 + y^2 >= 100 are
+ * skipped): a cell is validated when every checked point has
+ * |K_net - K_916| <= tol K_916.  Writes mask_host[cy*nx + cx] (0/1) and
+ * err_host (max relative error, -1 for cells with no point), both optional,
+ * and keeps the mask for routing.  Synchronises. */
+helk_status helk_surrogate_validate(helk_ctx *ctx, int32_t nx, int32_t ny,
+                                    int32_t per_cell, double tol,
+                                    uint8_t *mask_host, double *err_host);
 
 /* Transmission of every bin for nm column masses m (Sec. 2.1, Eq. for T:
  * T(m) = int_0^1 exp(-k(g) m) dg; the paper's "Transmission" stage).

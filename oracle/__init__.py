@@ -47,7 +47,9 @@ _p = ctypes.c_void_p
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # HELK_ORACLE_LIB: a deliberately broken build of the oracle, used by
+        # tests/test_oracle_mutations.py to show that the pins catch mistakes
+        path = os.environ.get("HELK_ORACLE_LIB") or _build.build()
         L = ctypes.CDLL(path)
         L.or_K916.restype = _d
         L.or_K916.argtypes = [_d, _d]

@@ -140,6 +140,10 @@ void helk_destroy(helk_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->mass_col) cudaFree(c->mass_col);
+  for (void *p : {(void *)c->mlp_p, (void *)c->mlp_m, (void *)c->mlp_v, (void *)c->mlp_g,
+                  (void *)c->mlp_loss, (void *)c->mlp_feat, (void *)c->mlp_tgt, (void *)c->mlp_mask,
+                  (void *)c->squeue, c->squeue_buf})
+    if (p) cudaFree(p);
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
                   c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
@@ -256,6 +260,10 @@ static helk_status check_condition(helk_ctx *c, double T, double P, double mass,
     return set_err(c, HELK_ERR_INVALID_ARG, "opts: unknown precision");
   if (!is_fin(o.weight) || !(is_fin(o.q_ratio) && o.q_ratio > 0.0))
     return set_err(c, HELK_ERR_INVALID_ARG, "opts: weight finite and q_ratio > 0 required");
+  if (o.surrogate && o.precision != HELK_PREC_F32_KAHAN)
+    return set_err(c, HELK_ERR_INVALID_ARG, "opts: the surrogate is used by the FP32 form only");
+  if (o.surrogate && !c->mlp_mask)
+    return set_err(c, HELK_ERR_STATE, "opts: surrogate requested but no network has been validated");
   return HELK_OK;
 }
 
@@ -266,6 +274,7 @@ static helk_opts default_opts() {
   o.weight = 1.0;
   o.q_ratio = 1.0;
   o.count_regions = 0;
+  o.surrogate = 0;
   return o;
 }
 
@@ -317,6 +326,27 @@ static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts 
     HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
                         "FP32 line records"));
   HELK_TRY(ensure_tiles(c, ntiles * n_cond));
+  if (o.surrogate && !c->squeue) {
+    // routed-evaluation queue: 2^24 entries (entries beyond it fall back to
+    // Algorithm 916 in the Voigt kernel)
+    const int64_t cap = (int64_t)1 << 24;
+    HELK_TRY(cuda_check(c, cudaMalloc(&c->squeue_buf, (size_t)cap * 20), "surrogate queue"));
+    HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->squeue, sizeof(SurrQueue)), "surrogate queue"));
+    SurrQueue q;
+    q.count = 0;
+    q.cap = (unsigned)cap;
+    char *b = (char *)c->squeue_buf;
+    q.idx = (int32_t *)b;
+    q.cond = (int32_t *)(b + cap * 4);
+    q.w = (float *)(b + cap * 8);
+    q.x = (float *)(b + cap * 12);
+    q.y = (float *)(b + cap * 16);
+    q.mask = c->mlp_mask;
+    q.nx = c->mlp_mask_nx;
+    q.ny = c->mlp_mask_ny;
+    HELK_TRY(cuda_check(c, cudaMemcpy(c->squeue, &q, sizeof q, cudaMemcpyHostToDevice), "surrogate queue"));
+    c->squeue_cap = cap;
+  }
   return HELK_OK;
 }
 
@@ -342,7 +372,10 @@ static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const 
   HELK_TRY(cuda_check(c, launch_cond_order(c, n_cond), "condition order"));
   HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->tile_counter, 0, sizeof(unsigned int), c->stream),
                       "voigt"));
+  if (o.surrogate)
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->squeue->count, 0, sizeof(unsigned int), c->stream), "voigt"));
   HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+  if (o.surrogate) HELK_TRY(cuda_check(c, launch_mlp_queue(c, n_cond, g->n, o.weight, kappa), "surrogate"));
   return HELK_OK;
 }
 
@@ -634,6 +667,194 @@ helk_status helk_transmission(helk_ctx *c, int32_t nbins, int64_t nb, const doub
   HELK_TRY(cuda_check(c, launch_transmission(c, nbins, nb, sorted, coeffs, ncheb, ng, nm, c->mass_col, direct, fit),
                       "transmission"));
   // m is pageable host memory: the copy above has completed when it returned
+  return HELK_OK;
+}
+
+// ------------------------------------------------------------ surrogate --
+static helk_status ensure_mlp(helk_ctx *c) {
+  if (c->mlp_p) return HELK_OK;
+  const size_t nb = MLP_NPARAMS_H * sizeof(float);
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_p, nb), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_m, nb), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_v, nb), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_g, nb), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_loss, 64), "surrogate"));
+  return HELK_OK;
+}
+
+static uint64_t splitmix64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+helk_status helk_surrogate_init(helk_ctx *c, uint64_t seed) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  HELK_TRY(bind_device(c));
+  HELK_TRY(ensure_mlp(c));
+  // He-style normal initialisation (Box-Muller on SplitMix64 variates)
+  std::vector<float> p(MLP_NPARAMS_H, 0.0f);
+  uint64_t st = seed;
+  auto normal = [&]() {
+    const double u1 = ((splitmix64(st) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = (splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * PI * u2);
+  };
+  const int H = 64;
+  for (int i = 0; i < 2 * H; ++i) p[i] = (float)(normal() * 1.0);                         // W1
+  for (int i = 0; i < H * H; ++i) p[192 + i] = (float)(normal() * sqrt(2.0 / H));          // W2
+  for (int i = 0; i < H * H; ++i) p[4352 + i] = (float)(normal() * sqrt(2.0 / H));         // W3
+  for (int i = 0; i < H; ++i) p[8512 + i] = (float)(normal() * sqrt(1.0 / H) * 0.1);       // W4
+  HELK_TRY(cuda_check(c, cudaMemcpy(c->mlp_p, p.data(), p.size() * 4, cudaMemcpyHostToDevice), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMemset(c->mlp_m, 0, p.size() * 4), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMemset(c->mlp_v, 0, p.size() * 4), "surrogate"));
+  c->mlp_step = 0;
+  return HELK_OK;
+}
+
+helk_status helk_surrogate_params(helk_ctx *c, float *get_host, const float *set_host) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  HELK_TRY(bind_device(c));
+  HELK_TRY(ensure_mlp(c));
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "surrogate"));
+  if (set_host) {
+    HELK_TRY(cuda_check(c, cudaMemcpy(c->mlp_p, set_host, MLP_NPARAMS_H * 4, cudaMemcpyHostToDevice), "surrogate"));
+    HELK_TRY(cuda_check(c, cudaMemset(c->mlp_m, 0, MLP_NPARAMS_H * 4), "surrogate"));
+    HELK_TRY(cuda_check(c, cudaMemset(c->mlp_v, 0, MLP_NPARAMS_H * 4), "surrogate"));
+    c->mlp_step = 0;
+  }
+  if (get_host)
+    HELK_TRY(cuda_check(c, cudaMemcpy(get_host, c->mlp_p, MLP_NPARAMS_H * 4, cudaMemcpyDeviceToHost), "surrogate"));
+  return HELK_OK;
+}
+
+static helk_status ensure_mlp_data(helk_ctx *c, int64_t n) {
+  if (n <= c->mlp_data_cap) return HELK_OK;
+  HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "surrogate data"));
+  if (c->mlp_feat) cudaFree(c->mlp_feat);
+  if (c->mlp_tgt) cudaFree(c->mlp_tgt);
+  c->mlp_feat = c->mlp_tgt = nullptr;
+  c->mlp_data_cap = 0;
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_feat, (size_t)n * 8), "surrogate data"));
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_tgt, (size_t)n * 4), "surrogate data"));
+  c->mlp_data_cap = n;
+  return HELK_OK;
+}
+
+helk_status helk_surrogate_samples(helk_ctx *c, int64_t n, uint64_t seed, float *feat, float *target,
+                                   double *x, double *y) {
+  if (!c || n < 1 || !feat || !target) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  HELK_TRY(bind_device(c));
+  return cuda_check(c, launch_mlp_samples(c, n, seed, feat, target, x, y), "surrogate samples");
+}
+
+helk_status helk_surrogate_grad(helk_ctx *c, int64_t n, const float *feat, const float *target, float *grad_host,
+                                double *loss_host) {
+  if (!c || n < 1 || !feat || !target) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->mlp_p) return set_err(c, HELK_ERR_STATE, "surrogate: no network (call helk_surrogate_init)");
+  HELK_TRY(bind_device(c));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->mlp_g, 0, MLP_NPARAMS_H * 4, c->stream), "surrogate"));
+  HELK_TRY(cuda_check(c, cudaMemsetAsync(c->mlp_loss, 0, 4, c->stream), "surrogate"));
+  HELK_TRY(cuda_check(c, launch_mlp_train_step(c, c->mlp_p, feat, target, 0, n, c->mlp_g, c->mlp_loss), "surrogate"));
+  HELK_TRY(helk_sync(c));
+  if (grad_host)
+    HELK_TRY(cuda_check(c, cudaMemcpy(grad_host, c->mlp_g, MLP_NPARAMS_H * 4, cudaMemcpyDeviceToHost), "surrogate"));
+  if (loss_host) {
+    float l = 0.f;
+    HELK_TRY(cuda_check(c, cudaMemcpy(&l, c->mlp_loss, 4, cudaMemcpyDeviceToHost), "surrogate"));
+    *loss_host = (double)l / (double)n;
+  }
+  return HELK_OK;
+}
+
+helk_status helk_surrogate_train(helk_ctx *c, int64_t n_samples, uint64_t seed, int32_t epochs, int32_t batch,
+                                 double lr, double *final_loss) {
+  if (!c || n_samples < 128 || epochs < 1 || batch < 128 || !(lr > 0.0)) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->mlp_p) return set_err(c, HELK_ERR_STATE, "surrogate: no network (call helk_surrogate_init)");
+  HELK_TRY(bind_device(c));
+  HELK_TRY(ensure_mlp_data(c, n_samples));
+  HELK_TRY(cuda_check(c, launch_mlp_samples(c, n_samples, seed, c->mlp_feat, c->mlp_tgt, nullptr, nullptr),
+                      "surrogate samples"));
+  const int64_t steps_per_epoch = n_samples / batch;
+  const int64_t total = steps_per_epoch * epochs;
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(c->mlp_loss, 0, 4, c->stream), "surrogate"));
+    for (int64_t s = 0; s < steps_per_epoch; ++s) {
+      // cosine decay of the learning rate to 1 % over the run
+      const double prog = (double)(ep * steps_per_epoch + s) / (double)std::max<int64_t>(1, total);
+      const float lr_s = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(PI * prog))));
+      HELK_TRY(cuda_check(c, cudaMemsetAsync(c->mlp_g, 0, MLP_NPARAMS_H * 4, c->stream), "surrogate"));
+      HELK_TRY(cuda_check(c, launch_mlp_train_step(c, c->mlp_p, c->mlp_feat, c->mlp_tgt, s * batch, batch,
+                                                   c->mlp_g, c->mlp_loss),
+                          "surrogate train"));
+      HELK_TRY(cuda_check(c, launch_mlp_adam(c, c->mlp_p, c->mlp_m, c->mlp_v, c->mlp_g, lr_s, ++c->mlp_step),
+                          "surrogate train"));
+    }
+    float l = 0.f;
+    HELK_TRY(cuda_check(c, cudaMemcpyAsync(&l, c->mlp_loss, 4, cudaMemcpyDeviceToHost, c->stream), "surrogate"));
+    HELK_TRY(helk_sync(c));
+    last = (double)l / (double)(steps_per_epoch * batch);
+  }
+  if (final_loss) *final_loss = last;
+  return HELK_OK;
+}
+
+helk_status helk_surrogate_eval(helk_ctx *c, int64_t n, const double *x, const double *y, double *k) {
+  if (!c || n < 0 || (n > 0 && (!x || !y || !k))) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->mlp_p) return set_err(c, HELK_ERR_STATE, "surrogate: no network (call helk_surrogate_init)");
+  HELK_TRY(bind_device(c));
+  return cuda_check(c, launch_mlp_eval(c, c->mlp_p, n, x, y, k), "surrogate eval");
+}
+
+helk_status helk_surrogate_validate(helk_ctx *c, int32_t nx, int32_t ny, int32_t per_cell, double tol,
+                                    uint8_t *mask_host, double *err_host) {
+  if (!c || nx < 1 || ny < 1 || nx * ny > 65536 || per_cell < 1 || per_cell > 64 || !(tol > 0.0))
+    return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->mlp_p) return set_err(c, HELK_ERR_STATE, "surrogate: no network (call helk_surrogate_init)");
+  HELK_TRY(bind_device(c));
+  const int ncell = nx * ny;
+  double *err = nullptr;
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&err, (size_t)ncell * 12 + 16), "surrogate validate"));
+  helk_status st = cuda_check(c, cudaMemsetAsync(err, 0, (size_t)ncell * 12 + 16, c->stream), "surrogate validate");
+  if (st == HELK_OK) st = cuda_check(c, launch_mlp_validate(c, nx, ny, per_cell, err), "surrogate validate");
+  std::vector<double> e(ncell);
+  std::vector<unsigned int> cnt(ncell);
+  if (st == HELK_OK) st = helk_sync(c);
+  if (st == HELK_OK) st = cuda_check(c, cudaMemcpy(e.data(), err, ncell * 8, cudaMemcpyDeviceToHost), "validate");
+  if (st == HELK_OK)
+    st = cuda_check(c, cudaMemcpy(cnt.data(), err + ncell, ncell * 4, cudaMemcpyDeviceToHost), "validate");
+  cudaFree(err);
+  HELK_TRY(st);
+  std::vector<uint32_t> bits((ncell + 31) / 32, 0u);
+  for (int i = 0; i < ncell; ++i) {
+    const bool ok = cnt[i] > 0 && e[i] <= tol;
+    if (ok) bits[i >> 5] |= 1u << (i & 31);
+    if (mask_host) mask_host[i] = ok ? 1 : 0;
+    if (err_host) err_host[i] = cnt[i] > 0 ? e[i] : -1.0;
+  }
+  if (c->mlp_mask) cudaFree(c->mlp_mask);
+  c->mlp_mask = nullptr;
+  HELK_TRY(cuda_check(c, cudaMalloc((void **)&c->mlp_mask, bits.size() * 4), "surrogate mask"));
+  HELK_TRY(cuda_check(c, cudaMemcpy(c->mlp_mask, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice), "mask"));
+  c->mlp_mask_nx = nx;
+  c->mlp_mask_ny = ny;
+  if (c->squeue) {  // point the routing queue at the new mask
+    SurrQueue q;
+    HELK_TRY(cuda_check(c, cudaMemcpy(&q, c->squeue, sizeof q, cudaMemcpyDeviceToHost), "mask"));
+    q.mask = c->mlp_mask;
+    q.nx = nx;
+    q.ny = ny;
+    HELK_TRY(cuda_check(c, cudaMemcpy(c->squeue, &q, sizeof q, cudaMemcpyHostToDevice), "mask"));
+  }
   return HELK_OK;
 }
 

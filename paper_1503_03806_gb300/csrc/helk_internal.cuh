@@ -77,6 +77,18 @@ struct DevStats {
   unsigned int tile_counter;        // next (condition, tile) item of the persistent Voigt kernel
 };
 
+// Core evaluations routed to the surrogate by the FP32 Voigt kernel: the
+// kernel appends (grid point, condition, scaled S', x, y); entries past
+// `cap` are evaluated in place by Algorithm 916 instead.
+struct SurrQueue {
+  unsigned int count;
+  unsigned int cap;
+  int32_t *idx, *cond;
+  float *w, *x, *y;
+  const uint32_t *mask;  // validated cells of the network, nx * ny bits
+  int nx, ny;
+};
+
 // One (T, P) condition of a call.
 struct CondArgs {
   double T, P, q_ratio, pad;
@@ -146,6 +158,18 @@ struct helk_ctx {
   int pinv_ncheb = 0;
   double *coef_dev = nullptr, *mean_dev = nullptr;
   int64_t coef_cap = 0, mean_cap = 0;
+  // Voigt surrogate network (k_mlp.cu): FP32 parameters, Adam moments,
+  // gradient, training set, validated-cell mask
+  float *mlp_p = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_g = nullptr, *mlp_loss = nullptr;
+  int mlp_step = 0;
+  float *mlp_feat = nullptr, *mlp_tgt = nullptr;
+  int64_t mlp_data_cap = 0;
+  uint32_t *mlp_mask = nullptr;  // bit c of word c/32: cell c validated
+  int mlp_mask_nx = 0, mlp_mask_ny = 0;
+  // queue of core evaluations routed to the network
+  helk::SurrQueue *squeue = nullptr;  // device struct
+  void *squeue_buf = nullptr;
+  int64_t squeue_cap = 0;
   // column masses of helk_transmission
   double *mass_col = nullptr;
   int64_t mass_col_cap = 0;
@@ -249,6 +273,18 @@ cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
                               double kappa_floor, double *coef, double *mean, double *kg_out);
 int64_t kdist_smem_max_points(helk_ctx *c);
+// k_mlp.cu
+constexpr int MLP_NPARAMS_H = 8577;
+cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const double *x, const double *y,
+                            double *k);
+cudaError_t launch_mlp_train_step(helk_ctx *c, const float *params, const float *feat, const float *tgt,
+                                  int64_t b0, int64_t B, float *grads, float *loss);
+cudaError_t launch_mlp_adam(helk_ctx *c, float *p, float *m, float *v, const float *grad, float lr, int step);
+cudaError_t launch_mlp_samples(helk_ctx *c, int64_t n, uint64_t seed, float *feat, float *tgt, double *xs,
+                               double *ys);
+cudaError_t launch_a916_points(helk_ctx *c, int64_t n, const double *x, const double *y, double *k);
+cudaError_t launch_mlp_validate(helk_ctx *c, int nx, int ny, int per_cell, double *err_dev);
+cudaError_t launch_mlp_queue(helk_ctx *c, int n_cond, int64_t ngrid, double weight, double *kappa);
 cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double *sorted,
                                 const double *coef, int ncheb, int ng, int nm, const double *m_dev,
                                 double *direct, double *fit);

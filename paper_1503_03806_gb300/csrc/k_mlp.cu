@@ -1,0 +1,639 @@
+// k_mlp.cu -- the Voigt-function surrogate: a 2 -> 64 -> 64 -> 64 -> 1 SiLU
+// network trained and evaluated with BF16 tensor-core MMAs (mma.sync
+// m16n8k16, FP32 accumulation).
+//
+// It stands in for K(x, y) = Re w(x + iy) where the method uses Algorithm 916
+// (Sec. 2.5: x^2 + y^2 < 100), as K = K_ref exp(net(f1, f2)) with
+//   K_ref = e^{-x^2} erfcx(y) + (1 - e^{-x^2}) y / (sqrt(pi)(x^2 + y^2)),
+//   f1 = 2 asinh|x| / asinh(10) - 1,  f2 = 2 (log10 y + 4) / 5 - 1,
+// so the network learns the residual ln(K / K_ref), |.| < 0.4.
+//
+// Precision: the 64 x 64 layers split activations and weights into BF16
+// high and low parts and accumulate hi*hi + hi*lo + lo*hi (relative error
+// ~2^-16 per product) in FP32; the 2 -> 64 input layer and the 64 -> 1 output
+// layer run in FP32 on the CUDA cores.  The backward pass uses plain BF16
+// MMAs.  Training targets come from this library's FP64 Algorithm 916
+// (itself held to the oracle at 1e-9), which also judges the network on a
+// held-out lattice; the network is used only in the cells where that check
+// passed.
+//
+// Fragment layouts of mma.m16n8k16 (lane = 4 g + t): A (16x16, row-major)
+// a0 = A[g][2t..2t+1], a1 = A[g+8][2t..], a2 = A[g][2t+8..], a3 = A[g+8][2t+8..];
+// B (16x8) b0 = B[2t..2t+1][g], b1 = B[2t+8..2t+9][g]; C (16x8) c0,c1 =
+// C[g][2t..2t+1], c2,c3 = C[g+8][2t..2t+1].  A warp holds the activations of
+// 16 samples as 8 C tiles (columns 8j + 2t + {0,1}), which are also the A
+// fragments of the next layer without data movement.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "helk_internal.cuh"
+#include "voigt_core.cuh"
+
+namespace helk {
+
+constexpr int MH = 64;  // hidden width
+constexpr int OFF_W1 = 0, OFF_B1 = 128, OFF_W2 = 192, OFF_B2 = 4288, OFF_W3 = 4352, OFF_B3 = 8448,
+              OFF_W4 = 8512, OFF_B4 = 8576;
+constexpr int MLP_NPARAMS = 8577;
+constexpr int WSTRIDE = 72;   // bf16 row stride of staged weights (bank-conflict free)
+constexpr int ASTRIDE = 136;  // bf16 row stride of the staged transposes (128 samples + 8)
+constexpr double ASINH_XCORE = 2.99822295029796973884;  // asinh(10)
+
+static_assert(OFF_B4 + 1 == MLP_NPARAMS, "parameter layout");
+
+// --------------------------------------------------------------- helpers --
+__device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi); both packed pairwise.
+__device__ __forceinline__ void split_pack(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+  const float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
+  __nv_bfloat162 h;
+  h.x = h0;
+  h.y = h1;
+  hi = *reinterpret_cast<uint32_t *>(&h);
+  lo = pack_bf16(r0, r1);
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float siluf_(float z) { return z * sigmoidf_(z); }
+__device__ __forceinline__ float dsiluf_(float z) {
+  const float s = sigmoidf_(z);
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// Features and reference function (FP64 arguments, as the sample generator
+// and the Voigt kernels hold them).
+__device__ __forceinline__ void mlp_features(double x, double y, float &f1, float &f2) {
+  f1 = (float)(2.0 * asinh(fabs(x)) / ASINH_XCORE - 1.0);
+  f2 = (float)(2.0 * (log10(y) + 4.0) / 5.0 - 1.0);
+}
+
+__device__ __forceinline__ double mlp_kref(double x, double y) {
+  const double e = exp(-x * x);
+  return e * erfcx(y) + (1.0 - e) * y / (SQRTPI * (x * x + y * y));
+}
+
+// --------------------------------------------------- staged parameters --
+struct MlpSmem {
+  __nv_bfloat16 wt_hi[2][MH * WSTRIDE];  // W2, W3 transposed [out][in], high part
+  __nv_bfloat16 wt_lo[2][MH * WSTRIDE];  // low part
+  __nv_bfloat16 wn[2][MH * WSTRIDE];     // W2, W3 [in][out] (backward)
+  float w1[2 * MH], b1[MH], b2[MH], b3[MH], w4[MH], b4;
+};
+
+__device__ void stage_params(const float *__restrict__ p, MlpSmem &S, bool backward) {
+  for (int e = threadIdx.x; e < MH * MH; e += blockDim.x) {
+    const int in = e / MH, out = e % MH;  // W[in][out]
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const float w = p[(l ? OFF_W3 : OFF_W2) + e];
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      S.wt_hi[l][out * WSTRIDE + in] = h;
+      S.wt_lo[l][out * WSTRIDE + in] = __float2bfloat16_rn(w - __bfloat162float(h));
+      if (backward) S.wn[l][in * WSTRIDE + out] = h;
+    }
+  }
+  for (int e = threadIdx.x; e < 2 * MH; e += blockDim.x) S.w1[e] = p[OFF_W1 + e];
+  for (int e = threadIdx.x; e < MH; e += blockDim.x) {
+    S.b1[e] = p[OFF_B1 + e];
+    S.b2[e] = p[OFF_B2 + e];
+    S.b3[e] = p[OFF_B3 + e];
+    S.w4[e] = p[OFF_W4 + e];
+  }
+  if (threadIdx.x == 0) S.b4 = p[OFF_B4];
+}
+
+// z = a W + b for one 64 x 64 layer of 16 samples; a given as FP32 C tiles.
+__device__ __forceinline__ void layer_split(const float a[8][4], const __nv_bfloat16 *wt_hi,
+                                            const __nv_bfloat16 *wt_lo, const float *bias, float z[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t ahi[4][4], alo[4][4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    split_pack(a[2 * s][0], a[2 * s][1], ahi[s][0], alo[s][0]);
+    split_pack(a[2 * s][2], a[2 * s][3], ahi[s][1], alo[s][1]);
+    split_pack(a[2 * s + 1][0], a[2 * s + 1][1], ahi[s][2], alo[s][2]);
+    split_pack(a[2 * s + 1][2], a[2 * s + 1][3], ahi[s][3], alo[s][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+    z[j][0] = b0;
+    z[j][1] = b1;
+    z[j][2] = b0;
+    z[j][3] = b1;
+    const int n = 8 * j + g;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int k = 16 * s + 2 * t;
+      const uint32_t bh0 = *reinterpret_cast<const uint32_t *>(&wt_hi[n * WSTRIDE + k]);
+      const uint32_t bh1 = *reinterpret_cast<const uint32_t *>(&wt_hi[n * WSTRIDE + k + 8]);
+      const uint32_t bl0 = *reinterpret_cast<const uint32_t *>(&wt_lo[n * WSTRIDE + k]);
+      const uint32_t bl1 = *reinterpret_cast<const uint32_t *>(&wt_lo[n * WSTRIDE + k + 8]);
+      mma16816(z[j], alo[s], bh0, bh1);
+      mma16816(z[j], ahi[s], bl0, bl1);
+      mma16816(z[j], ahi[s], bh0, bh1);
+    }
+  }
+}
+
+// Forward pass of 16 samples (rows g and g+8 of this lane's group); keeps the
+// pre-activations for the backward pass.  Returns the outputs of rows g, g+8.
+__device__ __forceinline__ void mlp_forward16(const MlpSmem &S, const float f[2][2], float z1[8][4],
+                                              float z2[8][4], float z3[8][4], float &out_g, float &out_g8) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  float a[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int col = 8 * j + 2 * t + c;
+      const float w0 = S.w1[col], w1 = S.w1[MH + col], b = S.b1[col];
+      z1[j][c] = fmaf(f[0][0], w0, fmaf(f[0][1], w1, b));
+      z1[j][2 + c] = fmaf(f[1][0], w0, fmaf(f[1][1], w1, b));
+    }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[j][c] = siluf_(z1[j][c]);
+  layer_split(a, S.wt_hi[0], S.wt_lo[0], S.b2, z2);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[j][c] = siluf_(z2[j][c]);
+  layer_split(a, S.wt_hi[1], S.wt_lo[1], S.b3, z3);
+  float pg = 0.0f, pg8 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float w = S.w4[8 * j + 2 * t + c];
+      pg = fmaf(siluf_(z3[j][c]), w, pg);
+      pg8 = fmaf(siluf_(z3[j][2 + c]), w, pg8);
+    }
+  pg += __shfl_xor_sync(0xffffffffu, pg, 1);
+  pg += __shfl_xor_sync(0xffffffffu, pg, 2);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
+  out_g = pg + S.b4;
+  out_g8 = pg8 + S.b4;
+}
+
+// ------------------------------------------------------------ inference --
+// K at n points (x, y): K_ref exp(net).  8 warps x 16 samples per CTA.
+__global__ void __launch_bounds__(256) k_mlp_eval(const float *__restrict__ params, int64_t n,
+                                                  const double *__restrict__ x, const double *__restrict__ y,
+                                                  double *__restrict__ kout) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  MlpSmem &S = *reinterpret_cast<MlpSmem *>(dsm);
+  stage_params(params, S, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; base < n;
+       base += (int64_t)gridDim.x * 128) {
+    const int64_t s0 = base + g, s1 = base + g + 8;
+    float f[2][2];
+    const double x0 = s0 < n ? x[s0] : 0.0, y0 = s0 < n ? y[s0] : 1.0;
+    const double x1 = s1 < n ? x[s1] : 0.0, y1 = s1 < n ? y[s1] : 1.0;
+    mlp_features(x0, y0, f[0][0], f[0][1]);
+    mlp_features(x1, y1, f[1][0], f[1][1]);
+    float z1[8][4], z2[8][4], z3[8][4], o0, o1;
+    mlp_forward16(S, f, z1, z2, z3, o0, o1);
+    if ((lane & 3) == 0) {
+      if (s0 < n) kout[s0] = mlp_kref(x0, y0) * exp((double)o0);
+      if (s1 < n) kout[s1] = mlp_kref(x1, y1) * exp((double)o1);
+    }
+  }
+}
+
+// ------------------------------------------------------------- training --
+// One minibatch: forward, loss, backward; gradients added to grads (FP32,
+// zeroed by the caller), the summed squared error to loss[0].  Samples
+// [b0, b0 + B) of the training set; 128 per CTA.
+struct TrainSmem {
+  MlpSmem m;
+  __nv_bfloat16 at[MH * ASTRIDE];  // activations, transposed [in][sample]
+  __nv_bfloat16 dt[MH * ASTRIDE];  // dz, transposed [out][sample]
+};
+
+// dW[i][o] += sum_s AT[i][s] DT[o][s] over the CTA's 128 samples; warp w
+// owns rows 16 (w/2) .. +16 and columns 32 (w%2) .. +32.
+__device__ __forceinline__ void cta_weight_grad(const TrainSmem &S, float *gW) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mt = w >> 1, nb = (w & 1) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks) {
+    const int k = 16 * ks + 2 * t;
+    const int r = 16 * mt + g;
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t *>(&S.at[r * ASTRIDE + k]);
+    a[1] = *reinterpret_cast<const uint32_t *>(&S.at[(r + 8) * ASTRIDE + k]);
+    a[2] = *reinterpret_cast<const uint32_t *>(&S.at[r * ASTRIDE + k + 8]);
+    a[3] = *reinterpret_cast<const uint32_t *>(&S.at[(r + 8) * ASTRIDE + k + 8]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = 8 * (nb + j) + g;
+      const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&S.dt[nn * ASTRIDE + k]);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&S.dt[nn * ASTRIDE + k + 8]);
+      mma16816(acc[j], a, b0, b1);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int col = 8 * (nb + j) + 2 * t;
+    const int row = 16 * mt + g;
+    atomicAdd(&gW[row * MH + col], acc[j][0]);
+    atomicAdd(&gW[row * MH + col + 1], acc[j][1]);
+    atomicAdd(&gW[(row + 8) * MH + col], acc[j][2]);
+    atomicAdd(&gW[(row + 8) * MH + col + 1], acc[j][3]);
+  }
+}
+
+// Stage a (FP32 C tiles of 16 samples) transposed into buf[in][16 w + row].
+__device__ __forceinline__ void stage_t(__nv_bfloat16 *buf, const float v[8][4]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int s0 = 16 * w + g;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int col = 8 * j + 2 * t + c;
+      buf[col * ASTRIDE + s0] = __float2bfloat16_rn(v[j][c]);
+      buf[col * ASTRIDE + s0 + 8] = __float2bfloat16_rn(v[j][2 + c]);
+    }
+}
+
+// Column sums of a C-tile array over the warp's 16 rows, added to g[64].
+__device__ __forceinline__ void add_colsum(float *gb, const float v[8][4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float s = v[j][c] + v[j][2 + c];
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 8);
+      s += __shfl_xor_sync(0xffffffffu, s, 16);
+      if ((lane >> 2) == 0) atomicAdd(&gb[8 * j + 2 * t + c], s);
+    }
+}
+
+// da = dz W^T for one 64 x 64 layer (BF16), W staged [in][out].
+__device__ __forceinline__ void layer_back(const float dz[8][4], const __nv_bfloat16 *wn, float da[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t a[4][4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    a[s][0] = pack_bf16(dz[2 * s][0], dz[2 * s][1]);
+    a[s][1] = pack_bf16(dz[2 * s][2], dz[2 * s][3]);
+    a[s][2] = pack_bf16(dz[2 * s + 1][0], dz[2 * s + 1][1]);
+    a[s][3] = pack_bf16(dz[2 * s + 1][2], dz[2 * s + 1][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    da[j][0] = da[j][1] = da[j][2] = da[j][3] = 0.0f;
+    const int n = 8 * j + g;  // input-unit index
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int k = 16 * s + 2 * t;  // output-unit index
+      const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&wn[n * WSTRIDE + k]);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&wn[n * WSTRIDE + k + 8]);
+      mma16816(da[j], a[s], b0, b1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mlp_train(const float *__restrict__ params,
+                                                   const float *__restrict__ feat, const float *__restrict__ tgt,
+                                                   int64_t b0, int64_t B, float *__restrict__ grads,
+                                                   float *__restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  TrainSmem &S = *reinterpret_cast<TrainSmem *>(dsm);
+  stage_params(params, S.m, true);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t r0 = (int64_t)blockIdx.x * 128 + 16 * w + g, r1 = r0 + 8;
+  const bool v0 = r0 < B, v1 = r1 < B;
+  float f[2][2];
+  f[0][0] = v0 ? feat[2 * (b0 + r0)] : 0.0f;
+  f[0][1] = v0 ? feat[2 * (b0 + r0) + 1] : 0.0f;
+  f[1][0] = v1 ? feat[2 * (b0 + r1)] : 0.0f;
+  f[1][1] = v1 ? feat[2 * (b0 + r1) + 1] : 0.0f;
+  float z1[8][4], z2[8][4], z3[8][4], o0, o1;
+  mlp_forward16(S.m, f, z1, z2, z3, o0, o1);
+  const float e0 = v0 ? o0 - tgt[b0 + r0] : 0.0f;
+  const float e1 = v1 ? o1 - tgt[b0 + r1] : 0.0f;
+  if (t == 0) atomicAdd(loss, e0 * e0 + e1 * e1);
+  const float d0 = 2.0f * e0 / (float)B, d1 = 2.0f * e1 / (float)B;
+  // output layer (FP32)
+  float dz[8][4], tmp[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int col = 8 * j + 2 * t + c;
+      tmp[j][c] = siluf_(z3[j][c]) * d0;
+      tmp[j][2 + c] = siluf_(z3[j][2 + c]) * d1;
+      dz[j][c] = d0 * S.m.w4[col] * dsiluf_(z3[j][c]);
+      dz[j][2 + c] = d1 * S.m.w4[col] * dsiluf_(z3[j][2 + c]);
+    }
+  add_colsum(grads + OFF_W4, tmp);
+  {
+    float s = (t == 0) ? d0 + d1 : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicAdd(&grads[OFF_B4], s);
+  }
+  // layer 3: dW3 = a2^T dz3, db3, da2 = dz3 W3^T
+  add_colsum(grads + OFF_B3, dz);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmp[j][c] = siluf_(z2[j][c]);
+  stage_t(S.at, tmp);
+  stage_t(S.dt, dz);
+  __syncthreads();
+  cta_weight_grad(S, grads + OFF_W3);
+  __syncthreads();
+  layer_back(dz, S.m.wn[1], tmp);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dz[j][c] = tmp[j][c] * dsiluf_(z2[j][c]);
+  // layer 2
+  add_colsum(grads + OFF_B2, dz);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmp[j][c] = siluf_(z1[j][c]);
+  stage_t(S.at, tmp);
+  stage_t(S.dt, dz);
+  __syncthreads();
+  cta_weight_grad(S, grads + OFF_W2);
+  __syncthreads();
+  layer_back(dz, S.m.wn[0], tmp);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dz[j][c] = tmp[j][c] * dsiluf_(z1[j][c]);
+  // layer 1 (FP32): dW1[f][o] = sum_s F[s][f] dz1[s][o]
+  add_colsum(grads + OFF_B1, dz);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        tmp[j][c] = f[0][q] * dz[j][c];
+        tmp[j][2 + c] = f[1][q] * dz[j][2 + c];
+      }
+    add_colsum(grads + OFF_W1 + q * MH, tmp);
+  }
+}
+
+// Adam step (Kingma & Ba 2015) on the FP32 master parameters.
+__global__ void k_mlp_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                           const float *__restrict__ grad, int n, float lr, float b1, float b2, float eps,
+                           float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gr = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gr;
+    const float vi = b2 * v[i] + (1.0f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// ------------------------------------------------------- training data --
+// Counter-based uniform variates: SplitMix64 (Steele, Lea & Flood 2014) of
+// (seed, sample, draw).
+__device__ __forceinline__ double u01(uint64_t seed, uint64_t i, uint64_t k) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i * 16 + k + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ double sig1_of(double y) {
+  double s = 0.0;
+  for (int k = 1; k <= A916_S1_TERMS; ++k) {
+    const double nh = k * A916_H;
+    s += exp(-nh * nh) / (nh * nh + y * y);
+  }
+  return s;
+}
+
+// Samples of the core region: |x| asinh-uniform in [0, 10], y log-uniform in
+// [1e-4, 10], redrawn until x^2 + y^2 < 100; features, the target
+// ln(K / K_ref) with K from Algorithm 916 in FP64, and x, y.
+__global__ void k_mlp_samples(int64_t n, uint64_t seed, float *__restrict__ feat, float *__restrict__ tgt,
+                              double *__restrict__ xs, double *__restrict__ ys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0.0, y = 1.0;
+    for (int k = 0; k < 8; ++k) {
+      x = sinh(u01(seed, i, 2 * k) * ASINH_XCORE);
+      y = pow(10.0, -4.0 + 5.0 * u01(seed, i, 2 * k + 1));
+      if (x * x + y * y < 100.0) break;
+    }
+    while (x * x + y * y >= 100.0) x *= 0.5;  // y < 10, so this ends
+    float f1, f2;
+    mlp_features(x, y, f1, f2);
+    const double K = k916_f64(x, y, erfcx(y), sig1_of(y));
+    feat[2 * i] = f1;
+    feat[2 * i + 1] = f2;
+    tgt[i] = (float)log(K / mlp_kref(x, y));
+    if (xs) xs[i] = x;
+    if (ys) ys[i] = y;
+  }
+}
+
+// Algorithm 916 (FP64) at given points: the judge of the network.
+__global__ void k_a916_points(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                              double *__restrict__ kout) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    kout[i] = k916_f64(fabs(x[i]), y[i], erfcx(y[i]), sig1_of(y[i]));
+}
+
+// ---------------------------------------------------------- validation --
+// Held-out check on a lattice: cell (cx, cy) of an nx x ny partition of the
+// feature square, per_cell^2 points at the sub-cell centres (never drawn by
+// the random training sampler); max relative error |K_net - K_916| / K_916
+// per cell (as ordered bits of a non-negative double), points with
+// x^2 + y^2 >= 100 skipped; cnt[cell] = points checked.
+__global__ void __launch_bounds__(256) k_mlp_validate(const float *__restrict__ params, int nx, int ny,
+                                                      int per, unsigned long long *__restrict__ err,
+                                                      unsigned int *__restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  MlpSmem &S = *reinterpret_cast<MlpSmem *>(dsm);
+  stage_params(params, S, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t n = (int64_t)nx * ny * per * per;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; base < n;
+       base += (int64_t)gridDim.x * 128) {
+    double xs[2], ys[2];
+    bool ok[2];
+    int cell[2];
+    float f[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t id = base + g + 8 * r;
+      const int64_t pc = per * per;
+      const int64_t cid = id / pc, sub = id % pc;
+      const int cx = (int)(cid % nx), cy = (int)(cid / nx);
+      const double f1 = -1.0 + 2.0 * (cx + ((sub % per) + 0.5) / per) / nx;
+      const double f2 = -1.0 + 2.0 * (cy + ((sub / per) + 0.5) / per) / ny;
+      xs[r] = sinh(0.5 * (f1 + 1.0) * ASINH_XCORE);
+      ys[r] = pow(10.0, 2.5 * (f2 + 1.0) - 4.0);
+      ok[r] = id < n && xs[r] * xs[r] + ys[r] * ys[r] < 100.0;
+      cell[r] = (int)cid;
+      mlp_features(xs[r], ys[r], f[r][0], f[r][1]);
+    }
+    float z1[8][4], z2[8][4], z3[8][4], o[2];
+    mlp_forward16(S, f, z1, z2, z3, o[0], o[1]);
+    if (t == 0) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!ok[r]) continue;
+        const double kn = mlp_kref(xs[r], ys[r]) * exp((double)o[r]);
+        const double ke = k916_f64(xs[r], ys[r], erfcx(ys[r]), sig1_of(ys[r]));
+        const double e = fabs(kn - ke) / ke;
+        atomicMax(&err[cell[r]], (unsigned long long)__double_as_longlong(e));
+        atomicAdd(&cnt[cell[r]], 1u);
+      }
+    }
+  }
+}
+
+// Routed core evaluations: K by the network, added (times the line's scaled
+// strength, the call weight and 2^E of its condition) into kappa.
+__global__ void __launch_bounds__(256) k_mlp_queue(const float *__restrict__ params, const SurrQueue *q,
+                                                   int64_t ngrid, double weight, const CondStats *__restrict__ cst,
+                                                   double *__restrict__ kappa) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  MlpSmem &S = *reinterpret_cast<MlpSmem *>(dsm);
+  const int64_t n = min(q->count, q->cap);
+  if ((int64_t)blockIdx.x * 128 >= n) return;
+  stage_params(params, S, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; base < n;
+       base += (int64_t)gridDim.x * 128) {
+    double xs[2], ys[2];
+    float f[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t e = base + g + 8 * r;
+      xs[r] = e < n ? (double)q->x[e] : 0.0;
+      ys[r] = e < n ? (double)q->y[e] : 1.0;
+      mlp_features(xs[r], ys[r], f[r][0], f[r][1]);
+    }
+    float z1[8][4], z2[8][4], z3[8][4], o[2];
+    mlp_forward16(S, f, z1, z2, z3, o[0], o[1]);
+    if (t == 0) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int64_t e = base + g + 8 * r;
+        if (e >= n) continue;
+        const int cond = q->cond[e];
+        const double K = mlp_kref(xs[r], ys[r]) * exp((double)o[r]);
+        atomicAdd(&kappa[(int64_t)cond * ngrid + q->idx[e]],
+                  ldexp(weight * (double)q->w[e] * K, cst[cond].scale_exp));
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- launch --
+cudaError_t launch_mlp_validate(helk_ctx *c, int nx, int ny, int per, double *err_dev) {
+  const size_t smem = sizeof(MlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)nx * ny * per * per;
+  int64_t blocks = (n + 127) / 128;
+  if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
+  unsigned int *cnt = reinterpret_cast<unsigned int *>(err_dev + (int64_t)nx * ny);
+  k_mlp_validate<<<(unsigned)blocks, 256, smem, c->stream>>>(
+      c->mlp_p, nx, ny, per, reinterpret_cast<unsigned long long *>(err_dev), cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_queue(helk_ctx *c, int n_cond, int64_t ngrid, double weight, double *kappa) {
+  (void)n_cond;
+  const size_t smem = sizeof(MlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (c->squeue_cap + 127) / 128;
+  if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
+  if (blocks < 1) blocks = 1;
+  k_mlp_queue<<<(unsigned)blocks, 256, smem, c->stream>>>(c->mlp_p, c->squeue, ngrid, weight, c->cstats, kappa);
+  return cudaGetLastError();
+}
+
+size_t mlp_eval_smem() { return sizeof(MlpSmem); }
+size_t mlp_train_smem() { return sizeof(TrainSmem); }
+
+cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const double *x, const double *y,
+                            double *k) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = sizeof(MlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n + 127) / 128;
+  if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
+  k_mlp_eval<<<(unsigned)blocks, 256, smem, c->stream>>>(params, n, x, y, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train_step(helk_ctx *c, const float *params, const float *feat, const float *tgt,
+                                  int64_t b0, int64_t B, float *grads, float *loss) {
+  const size_t smem = sizeof(TrainSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_mlp_train<<<(unsigned)((B + 127) / 128), 256, smem, c->stream>>>(params, feat, tgt, b0, B, grads, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_adam(helk_ctx *c, float *p, float *m, float *v, const float *grad, float lr, int step) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  k_mlp_adam<<<34, 256, 0, c->stream>>>(p, m, v, grad, MLP_NPARAMS, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_samples(helk_ctx *c, int64_t n, uint64_t seed, float *feat, float *tgt, double *xs,
+                               double *ys) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  k_mlp_samples<<<(unsigned)blocks, 256, 0, c->stream>>>(n, seed, feat, tgt, xs, ys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_a916_points(helk_ctx *c, int64_t n, const double *x, const double *y, double *k) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  k_a916_points<<<(unsigned)blocks, 256, 0, c->stream>>>(n, x, y, k);
+  return cudaGetLastError();
+}
+
+}  // namespace helk

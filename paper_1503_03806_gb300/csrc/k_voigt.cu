@@ -25,96 +25,11 @@
 #include <algorithm>
 
 #include "helk_internal.cuh"
+#include "voigt_core.cuh"
 
 namespace helk {
 
 constexpr long long WAIT_LIMIT = 1ll << 24;  // polls of a bulk-copy barrier
-
-// ------------------------------------------------------------------------
-// Algorithm 916 (Sec. 2.5), FP64.  K(x, y) for 0 <= x, x^2 + y^2 < 100:
-//   K = e^{-x^2} erfcx(y) cos(2xy) + (2hx/pi) e^{-x^2} sin(xy) sinc(xy)
-//     + (2h/pi) [ -y cos(2xy) e^{-x^2} S1 + (y/2)(S2 + S3) ],
-//   S1 = sum e^{-(nh)^2}/((nh)^2+y^2)  (per line: sig1),
-//   S2 + S3 = sum (e^{-(nh+x)^2} + e^{-(nh-x)^2}) / ((nh)^2 + y^2),
-// the exponentials of S2/S3 advanced by the exact ratio recurrences
-//   e^{-((n+1)h -+ x)^2} = e^{-(nh -+ x)^2} * R,  R <- R e^{-2h^2}.
-// Only the terms within A916_TAIL of the Gaussian peaks are summed.
-__device__ __forceinline__ void a916_range(double x, int &n0, int &n1) {
-  n0 = (int)floor((x - A916_TAIL) / A916_H);
-  if (n0 < 1) n0 = 1;
-  n1 = (int)ceil((x + A916_TAIL) / A916_H);
-}
-
-__device__ __noinline__ double k916_f64(double x, double y, double erfcx_y, double sig1) {
-  const double h = A916_H;
-  const double ex2 = exp(-(x * x));
-  const double xy = x * y;
-  double s, c;
-  sincos(xy, &s, &c);
-  const double sinc = (xy == 0.0) ? 1.0 : s / xy;
-  const double c2xy = c * c - s * s;
-  int n0, n1;
-  a916_range(x, n0, n1);
-  const double q = 0.60653065971263342360;  // e^{-2h^2}
-  const double nh = n0 * h;
-  const double dm = nh - x, dp = nh + x;
-  double E3 = exp(-(dm * dm));
-  double R3 = exp(-(2.0 * h * dm + h * h));
-  double E2 = exp(-(dp * dp));
-  double R2 = exp(-(2.0 * h * dp + h * h));
-  double s23 = 0.0;
-  const double y2 = y * y;
-  for (int n = n0; n <= n1; ++n) {
-    const double nhn = n * h;
-    s23 += (E2 + E3) / (nhn * nhn + y2);
-    E3 *= R3;
-    R3 *= q;
-    E2 *= R2;
-    R2 *= q;
-  }
-  double K = ex2 * erfcx_y * c2xy;
-  K += (2.0 * h / PI) * x * ex2 * s * sinc;
-  K += (2.0 * h / PI) * (0.5 * y * s23 - y * c2xy * ex2 * sig1);
-  return K;
-}
-
-// The same series in FP32 (accurate expf/sincosf; recurrences start at the
-// low end of the summed range, where the terms are ~e^{-38}, so nothing
-// overflows or underflows in FP32).
-__device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
-  const float h = 0.5f;
-  const float ex2 = expf(-(x * x));
-  const float xy = x * y;
-  float s, c;
-  sincosf(xy, &s, &c);
-  const float sinc = (xy == 0.0f) ? 1.0f : s / xy;
-  const float c2xy = c * c - s * s;
-  int n0 = (int)floorf((x - 6.2f) * 2.0f);
-  if (n0 < 1) n0 = 1;
-  const int n1 = (int)ceilf((x + 6.2f) * 2.0f);
-  const float q = 0.60653065971f;  // e^{-2h^2}
-  const float nh = n0 * h;
-  const float dm = nh - x, dp = nh + x;
-  float E3 = expf(-(dm * dm));
-  float R3 = expf(-(2.0f * h * dm + h * h));
-  float E2 = expf(-(dp * dp));
-  float R2 = expf(-(2.0f * h * dp + h * h));
-  float s23 = 0.0f;
-  const float y2 = y * y;
-  for (int n = n0; n <= n1; ++n) {
-    const float nhn = n * h;
-    s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
-    E3 *= R3;
-    R3 *= q;
-    E2 *= R2;
-    R2 *= q;
-  }
-  const float k2h = 0.31830988618f;  // 2h/pi
-  float K = ex2 * erfcx_y * c2xy;
-  K += k2h * x * ex2 * s * sinc;
-  K += k2h * (0.5f * y * s23 - y * c2xy * ex2 * sig1);
-  return K;
-}
 
 // Reciprocal of a double x >= 100: FP32 hardware seed (relative error
 // < 2^-22) refined by one Newton step, relative error < 1e-13 -- far inside
@@ -304,6 +219,19 @@ enum { CLS_GH1 = 0, CLS_GH3 = 1, CLS_MIXED = 2 };
 constexpr float F32_T1SQ = 1.5f;            // square of the GH3 node sqrt(3/2)
 constexpr int KAHAN_GROUP = 8;              // lines per compensated partial
 
+// Whether a core evaluation at (x, y) lies in a cell where the surrogate
+// network was validated (features as in k_mlp.cu).
+__device__ __forceinline__ bool surr_route(const SurrQueue *sq, float x, float y) {
+  if (!(y >= 1.0e-4f && y < 10.0f)) return false;
+  const float f1 = 2.0f * asinhf(x) * 0.33352f - 1.0f;  // 1/asinh(10)
+  const float f2 = 0.4f * (log10f(y) + 4.0f) - 1.0f;
+  int cx = (int)((f1 + 1.0f) * 0.5f * sq->nx), cy = (int)((f2 + 1.0f) * 0.5f * sq->ny);
+  cx = min(max(cx, 0), sq->nx - 1);
+  cy = min(max(cy, 0), sq->ny - 1);
+  const int cell = cy * sq->nx + cx;
+  return (sq->mask[cell >> 5] >> (cell & 31)) & 1u;
+}
+
 // Hardware reciprocal approximation (max relative error ~1 ulp); every
 // argument here is >= 100, far from the denormal range.
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -336,7 +264,7 @@ __global__ void __launch_bounds__(BLOCK)
                 const int32_t *__restrict__ tlo_all, const int32_t *__restrict__ thi_all,
                 int64_t ntiles, const int *__restrict__ cond_order, int n_cond, int ngrid,
                 double weight, int accumulate, double *__restrict__ kappa_all, CondStats *cst,
-                DevStats *st) {
+                DevStats *st, SurrQueue *sq) {
   // Warp w of the CTA owns the WSPAN consecutive points starting at
   // base + w WSPAN; lane l holds points base + w WSPAN + 32 k + l.  Method
   // classes are decided per (line, warp), so only the warps whose span holds
@@ -457,7 +385,21 @@ __global__ void __launch_bounds__(BLOCK)
               v = gh3_term(u, r2, P3h);
               if (COUNT) cnt[1]++;
             } else {
-              v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+              if (sq && surr_route(sq, fabsf(u), buf[j].a)) {
+                const unsigned slot = atomicAdd(&sq->count, 1u);
+                if (slot < sq->cap) {
+                  sq->idx[slot] = i;
+                  sq->cond[slot] = cond;
+                  sq->w[slot] = buf[j].Sp;
+                  sq->x[slot] = fabsf(u);
+                  sq->y[slot] = buf[j].a;
+                  v = 0.0f;
+                } else {
+                  v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+                }
+              } else {
+                v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+              }
               if (COUNT) {
                 int n0, n1;
                 a916_range(fabs((double)u), n0, n1);
@@ -586,6 +528,7 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
                          double *kappa, int tile_len, int64_t ntiles) {
   const int64_t nitems = ntiles * n_cond;
   if (o.precision == HELK_PREC_F32_KAHAN) {
+    SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
     const int ns = tile_len / F32_BLOCK;
 #define X(NS)                                                                                   \
     if (ns == NS) {                                                                             \
@@ -593,12 +536,12 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
         auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, true>;                                   \
         kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
             c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
-            o.weight, o.accumulate, kappa, c->cstats, c->stats);                                 \
+            o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                             \
       } else {                                                                                  \
         auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false>;                                  \
         kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
             c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
-            o.weight, o.accumulate, kappa, c->cstats, c->stats);                                 \
+            o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                             \
       }                                                                                         \
       return cudaGetLastError();                                                                \
     }

@@ -1,0 +1,98 @@
+// voigt_core.cuh -- device functions of Algorithm 916 shared by the Voigt
+// kernels and the surrogate's training-target kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "helk_internal.cuh"
+
+namespace helk {
+
+// ------------------------------------------------------------------------
+// Algorithm 916 (Sec. 2.5), FP64.  K(x, y) for 0 <= x, x^2 + y^2 < 100:
+//   K = e^{-x^2} erfcx(y) cos(2xy) + (2hx/pi) e^{-x^2} sin(xy) sinc(xy)
+//     + (2h/pi) [ -y cos(2xy) e^{-x^2} S1 + (y/2)(S2 + S3) ],
+//   S1 = sum e^{-(nh)^2}/((nh)^2+y^2)  (per line: sig1),
+//   S2 + S3 = sum (e^{-(nh+x)^2} + e^{-(nh-x)^2}) / ((nh)^2 + y^2),
+// the exponentials of S2/S3 advanced by the exact ratio recurrences
+//   e^{-((n+1)h -+ x)^2} = e^{-(nh -+ x)^2} * R,  R <- R e^{-2h^2}.
+// Only the terms within A916_TAIL of the Gaussian peaks are summed.
+static __device__ __forceinline__ void a916_range(double x, int &n0, int &n1) {
+  n0 = (int)floor((x - A916_TAIL) / A916_H);
+  if (n0 < 1) n0 = 1;
+  n1 = (int)ceil((x + A916_TAIL) / A916_H);
+}
+
+static __device__ __noinline__ double k916_f64(double x, double y, double erfcx_y, double sig1) {
+  const double h = A916_H;
+  const double ex2 = exp(-(x * x));
+  const double xy = x * y;
+  double s, c;
+  sincos(xy, &s, &c);
+  const double sinc = (xy == 0.0) ? 1.0 : s / xy;
+  const double c2xy = c * c - s * s;
+  int n0, n1;
+  a916_range(x, n0, n1);
+  const double q = 0.60653065971263342360;  // e^{-2h^2}
+  const double nh = n0 * h;
+  const double dm = nh - x, dp = nh + x;
+  double E3 = exp(-(dm * dm));
+  double R3 = exp(-(2.0 * h * dm + h * h));
+  double E2 = exp(-(dp * dp));
+  double R2 = exp(-(2.0 * h * dp + h * h));
+  double s23 = 0.0;
+  const double y2 = y * y;
+  for (int n = n0; n <= n1; ++n) {
+    const double nhn = n * h;
+    s23 += (E2 + E3) / (nhn * nhn + y2);
+    E3 *= R3;
+    R3 *= q;
+    E2 *= R2;
+    R2 *= q;
+  }
+  double K = ex2 * erfcx_y * c2xy;
+  K += (2.0 * h / PI) * x * ex2 * s * sinc;
+  K += (2.0 * h / PI) * (0.5 * y * s23 - y * c2xy * ex2 * sig1);
+  return K;
+}
+
+// The same series in FP32 (accurate expf/sincosf; recurrences start at the
+// low end of the summed range, where the terms are ~e^{-38}, so nothing
+// overflows or underflows in FP32).
+static __device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
+  const float h = 0.5f;
+  const float ex2 = expf(-(x * x));
+  const float xy = x * y;
+  float s, c;
+  sincosf(xy, &s, &c);
+  const float sinc = (xy == 0.0f) ? 1.0f : s / xy;
+  const float c2xy = c * c - s * s;
+  int n0 = (int)floorf((x - 6.2f) * 2.0f);
+  if (n0 < 1) n0 = 1;
+  const int n1 = (int)ceilf((x + 6.2f) * 2.0f);
+  const float q = 0.60653065971f;  // e^{-2h^2}
+  const float nh = n0 * h;
+  const float dm = nh - x, dp = nh + x;
+  float E3 = expf(-(dm * dm));
+  float R3 = expf(-(2.0f * h * dm + h * h));
+  float E2 = expf(-(dp * dp));
+  float R2 = expf(-(2.0f * h * dp + h * h));
+  float s23 = 0.0f;
+  const float y2 = y * y;
+  for (int n = n0; n <= n1; ++n) {
+    const float nhn = n * h;
+    s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
+    E3 *= R3;
+    R3 *= q;
+    E2 *= R2;
+    R2 *= q;
+  }
+  const float k2h = 0.31830988618f;  // 2h/pi
+  float K = ex2 * erfcx_y * c2xy;
+  K += k2h * x * ex2 * s * sinc;
+  K += k2h * (0.5f * y * s23 - y * c2xy * ex2 * sig1);
+  return K;
+}
+
+}  // namespace helk

@@ -44,7 +44,7 @@ class helk_lines(ctypes.Structure):
 class helk_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("accumulate", ctypes.c_int32),
                 ("weight", ctypes.c_double), ("q_ratio", ctypes.c_double),
-                ("count_regions", ctypes.c_int32)]
+                ("count_regions", ctypes.c_int32), ("surrogate", ctypes.c_int32)]
 
 
 LINE_FIELDS = ("nu0", "S0", "E_lower", "gamma_air", "gamma_self", "n_coll", "delta", "mass",
@@ -73,11 +73,19 @@ SIGNATURES = [
                                           ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts), _P]),
     ("helk_opacity_batch_stats", ctypes.c_int, [_P, _I32, _P, _P]),
     ("helk_transmission", ctypes.c_int, [_P, _I32, _I64, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    ("helk_surrogate_init", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("helk_surrogate_params", ctypes.c_int, [_P, _P, _P]),
+    ("helk_surrogate_samples", ctypes.c_int, [_P, _I64, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("helk_surrogate_grad", ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
+    ("helk_surrogate_train", ctypes.c_int, [_P, _I64, ctypes.c_uint64, _I32, _I32, _D, _P]),
+    ("helk_surrogate_eval", ctypes.c_int, [_P, _I64, _P, _P, _P]),
+    ("helk_surrogate_validate", ctypes.c_int, [_P, _I32, _I32, _I32, _D, _P, _P]),
     ("helk_autotune", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(helk_cutoff),
                                      ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
                                      ctypes.POINTER(_I32)]),
 ]
 HELK_NSTAGES = 4
+MLP_NPARAMS = 8577
 STAGE_NAMES = ("lineprep", "voigt", "kdist", "setup")
 
 
@@ -246,7 +254,7 @@ class Context:
         self.nlines = n or 0
 
     def opacity(self, T, P, mass, cut, grid, out=None, precision=HELK_PREC_F64, accumulate=False,
-                weight=1.0, q_ratio=1.0, count_regions=False):
+                weight=1.0, q_ratio=1.0, count_regions=False, surrogate=False):
         """grid = (nu_min, dnu, n).  Returns the kappa tensor (float64)."""
         torch = self.torch
         g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
@@ -254,12 +262,12 @@ class Context:
             out = torch.empty(int(grid[2]), dtype=torch.float64, device=self.device)
         assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous()
         o = helk_opts(int(precision), int(bool(accumulate)), float(weight), float(q_ratio),
-                      int(bool(count_regions)))
+                      int(bool(count_regions)), int(bool(surrogate)))
         _check(self.h, helk_opacity(self.h, T, P, mass, _cut(cut), g, o, ctypes.c_void_p(out.data_ptr())))
         return out
 
     def opacity_batch(self, T, P, mass, cut, grid, out=None, precision=HELK_PREC_F64, q_ratio=None,
-                      accumulate=False, weight=1.0, count_regions=False):
+                      accumulate=False, weight=1.0, count_regions=False, surrogate=False):
         """n_cond conditions (T[k], P[k]) in one graph-captured persistent launch;
         returns kappa as a (n_cond, n) float64 tensor."""
         torch = self.torch
@@ -271,7 +279,8 @@ class Context:
         if out is None:
             out = torch.empty((nc, int(grid[2])), dtype=torch.float64, device=self.device)
         assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous()
-        o = helk_opts(int(precision), int(bool(accumulate)), float(weight), 1.0, int(bool(count_regions)))
+        o = helk_opts(int(precision), int(bool(accumulate)), float(weight), 1.0, int(bool(count_regions)),
+                      int(bool(surrogate)))
         _check(self.h, lib.helk_opacity_batch(self.h, nc, T.ctypes.data_as(_P), P.ctypes.data_as(_P),
                                               None if q is None else q.ctypes.data_as(_P), float(mass),
                                               ctypes.byref(_cut(cut)), ctypes.byref(g), ctypes.byref(o),
@@ -306,11 +315,62 @@ class Context:
         """Time the built Voigt tile shapes on this condition; keep the
         fastest for later calls with the same precision and grid size."""
         g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
-        o = helk_opts(int(precision), 0, 1.0, float(q_ratio), 0)
+        o = helk_opts(int(precision), 0, 1.0, float(q_ratio), 0, 0)
         t = _I32(0)
         _check(self.h, lib.helk_autotune(self.h, float(T), float(P), float(mass), ctypes.byref(_cut(cut)),
                                          ctypes.byref(g), ctypes.byref(o), ctypes.byref(t)))
         return int(t.value)
+
+    # ------------------------------------------------------ surrogate --
+    def surrogate_init(self, seed=0):
+        _check(self.h, lib.helk_surrogate_init(self.h, int(seed)))
+
+    def surrogate_params(self, new=None):
+        """Current parameters (numpy float32, 8577); replaces them first if new."""
+        out = np.empty(MLP_NPARAMS, dtype=np.float32)
+        src = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        _check(self.h, lib.helk_surrogate_params(self.h, out.ctypes.data_as(_P),
+                                                 None if src is None else src.ctypes.data_as(_P)))
+        return out
+
+    def surrogate_samples(self, n, seed):
+        torch = self.torch
+        feat = torch.empty((n, 2), dtype=torch.float32, device=self.device)
+        tgt = torch.empty(n, dtype=torch.float32, device=self.device)
+        x = torch.empty(n, dtype=torch.float64, device=self.device)
+        y = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(self.h, lib.helk_surrogate_samples(self.h, int(n), int(seed), ctypes.c_void_p(feat.data_ptr()),
+                                                  ctypes.c_void_p(tgt.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(y.data_ptr())))
+        return feat, tgt, x, y
+
+    def surrogate_grad(self, feat, tgt):
+        g = np.empty(MLP_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(self.h, lib.helk_surrogate_grad(self.h, int(tgt.numel()), ctypes.c_void_p(feat.data_ptr()),
+                                               ctypes.c_void_p(tgt.data_ptr()), g.ctypes.data_as(_P),
+                                               ctypes.byref(loss)))
+        return g, loss.value
+
+    def surrogate_train(self, n_samples, seed, epochs, batch=4096, lr=2e-3):
+        loss = ctypes.c_double(0.0)
+        _check(self.h, lib.helk_surrogate_train(self.h, int(n_samples), int(seed), int(epochs), int(batch),
+                                                float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def surrogate_eval(self, x, y):
+        torch = self.torch
+        k = torch.empty_like(x)
+        _check(self.h, lib.helk_surrogate_eval(self.h, int(x.numel()), ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(k.data_ptr())))
+        return k
+
+    def surrogate_validate(self, nx=32, ny=32, per_cell=6, tol=1e-4):
+        mask = np.zeros(nx * ny, dtype=np.uint8)
+        err = np.zeros(nx * ny)
+        _check(self.h, lib.helk_surrogate_validate(self.h, nx, ny, per_cell, float(tol),
+                                                   mask.ctypes.data_as(_P), err.ctypes.data_as(_P)))
+        return mask.reshape(ny, nx), err.reshape(ny, nx)
 
     def set_profiling(self, on):
         helk_set_profiling(self.h, on)

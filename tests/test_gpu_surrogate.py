@@ -1,0 +1,149 @@
+"""The BF16 tensor-core surrogate network for the Voigt function.
+
+- forward pass against the FP64 reference network (oracle/mlp.py) with the
+  same weights: the hi/lo BF16 split gives ~2^-16 relative per product, so
+  the bar is 5e-5 relative on K;
+- loss gradient of one minibatch against the FP64 reference: the backward
+  pass uses plain BF16 operands (2^-9), so the bar is 5e-3 of the gradient's
+  norm (and cosine > 0.9999);
+- training on the library's own samples lowers the loss and validates
+  cells; cells are validated at 5e-5 on an 8 x 8 lattice per cell, a 2x
+  margin so that random held-out points of validated cells stay within the
+  surrogate form's 1e-4 against the exact w(z) (scipy);
+- the FP32 form with routing stays within the surrogate form's stated error
+  (1e-4 where kappa > 1e-8 of its bin maximum) against the FP64 oracle, and
+  beats the plain FP64 form on a core-dominated workload.
+The inputs checked against the oracle are drawn here with numpy; the
+network's own training data come from the library (FP64 Algorithm 916).
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1503_03806_gb300 import synth
+from tests.helpers import NTHREADS, Case
+
+pytestmark = pytest.mark.gpu
+
+scipy_special = pytest.importorskip("scipy.special")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_03806_gb300 import build
+    build.build()
+    from paper_1503_03806_gb300 import helk
+    c = helk.Context(0)
+    yield c
+    c.close()
+
+
+def core_points(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.sinh(rng.uniform(0, math.asinh(10.0), n))
+    y = 10 ** rng.uniform(-4, 1, n)
+    keep = x * x + y * y < 100
+    return x[keep], y[keep]
+
+
+def test_forward_matches_reference_network(ctx):
+    import torch
+    p = mlp.init_params(1).astype(np.float32)
+    ctx.surrogate_params(p)
+    x, y = core_points(5000, 2)
+    k = ctx.surrogate_eval(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+    ref = mlp.predict_k(p.astype(np.float64), x, y)
+    assert np.max(np.abs(k / ref - 1)) < 5e-5
+
+
+def test_gradient_matches_reference(ctx):
+    import torch
+    p = mlp.init_params(3).astype(np.float32)
+    ctx.surrogate_params(p)
+    x, y = core_points(3000, 4)
+    F = mlp.features(x, y)
+    t = np.log(scipy_special.wofz(x + 1j * y).real / mlp.k_ref(x, y))
+    g, loss = ctx.surrogate_grad(torch.from_numpy(F.astype(np.float32)).cuda(),
+                                 torch.from_numpy(t.astype(np.float32)).cuda())
+    loss_or, g_or = mlp.loss_and_grad(p.astype(np.float64), F, t)
+    assert abs(loss - loss_or) <= 1e-4 * loss_or
+    assert np.linalg.norm(g - g_or) <= 5e-3 * np.linalg.norm(g_or)
+    assert g @ g_or / (np.linalg.norm(g) * np.linalg.norm(g_or)) > 0.9999
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    ctx.surrogate_init(7)
+    loss = ctx.surrogate_train(10_000_000, 11, 30, batch=4096, lr=3e-3)
+    mask, err = ctx.surrogate_validate(32, 32, 8, 5e-5)
+    return loss, mask, err
+
+
+def test_training_validates_cells(ctx, trained):
+    import torch
+    loss, mask, err = trained
+    assert loss < 1e-7
+    checked = err >= 0
+    assert mask.sum() > 0.2 * checked.sum(), (mask.sum(), checked.sum())
+    assert np.all(err[mask.astype(bool)] <= 5e-5)
+    # random held-out points inside validated cells, against the exact w(z)
+    x, y = core_points(20000, 9)
+    F = mlp.features(x, y)
+    cx = np.clip(((F[:, 0] + 1) / 2 * 32).astype(int), 0, 31)
+    cy = np.clip(((F[:, 1] + 1) / 2 * 32).astype(int), 0, 31)
+    sel = mask[cy, cx].astype(bool)
+    k = ctx.surrogate_eval(torch.from_numpy(x[sel]).cuda(), torch.from_numpy(y[sel]).cuda()).cpu().numpy()
+    exact = scipy_special.wofz(x[sel] + 1j * y[sel]).real
+    assert np.max(np.abs(k / exact - 1)) < 1e-4
+
+
+def core_dominated_case():
+    # low pressure and a tight cutoff: nearly every evaluation is in the
+    # Algorithm 916 region
+    lines = synth.random_lines(3000, 601, 10000.0, 10300.0)
+    case = Case(1500.0, 0.01, 18.0, (10000.0, 0.001, 300_000), ("abs", 0.3))
+    return lines, case
+
+
+def test_routed_opacity_within_surrogate_error(ctx, trained):
+    from paper_1503_03806_gb300 import helk
+    lines, case = core_dominated_case()
+    ctx.upload(lines)
+    k_plain = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN, count_regions=True).cpu().numpy()
+    ev, reg = ctx.stats(with_regions=True)
+    assert reg[0] > 0.9 * ev
+    k_s = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN, surrogate=True).cpu().numpy()
+    assert not np.array_equal(k_s, k_plain)  # evaluations were routed
+    ko, _, _ = oracle.opacity(lines, case.oracle_cond(), nthreads=NTHREADS)
+    g, r = k_s.reshape(30, -1), ko.reshape(30, -1)
+    sel = r > 1e-8 * r.max(axis=1, keepdims=True)
+    assert np.max(np.abs(g[sel] / r[sel] - 1)) < 1e-4
+
+
+def test_surrogate_form_beats_fp64_form(ctx, trained):
+    import torch
+    from paper_1503_03806_gb300 import helk
+    lines, case = core_dominated_case()
+    ctx.upload(lines)
+
+    def timed(**kw):
+        case.gpu(ctx, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            case.gpu(ctx, **kw)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / 3
+
+    t64 = timed(precision=helk.HELK_PREC_F64)
+    t32 = timed(precision=helk.HELK_PREC_F32_KAHAN)
+    ts = timed(precision=helk.HELK_PREC_F32_KAHAN, surrogate=True)
+    print("core-dominated opacity: FP64 %.3f ms, FP32 %.3f ms, FP32+surrogate %.3f ms"
+          % (t64 * 1e3, t32 * 1e3, ts * 1e3))
+    assert ts < t64
