@@ -58,6 +58,25 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def rank_temperature(w, rank, world):
+    """The condition rank `rank` of `world` runs (weak scaling: every rank
+    runs the full workload at its own temperature; one rank runs the
+    workload's own)."""
+    import numpy as np
+    return w["T"][0] if world == 1 else float(np.linspace(500.0, 3000.0, world)[rank])
+
+
+def max_over_ranks(value, dist, device):
+    """Max of a per-rank scalar (step times are reported as the slowest
+    rank's); the one collective of the benchmark, outside the data path."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -216,7 +235,7 @@ def run_ours(args):
     from paper_1503_03806_gb300 import helk, synth
 
     w = synth.WORKLOADS[WORKLOAD]
-    T = w["T"][0] if world == 1 else float(np.linspace(500.0, 3000.0, world)[rank])
+    T = rank_temperature(w, rank, world)
     P, mass, cut = w["P_atm"][0], w["mass"], w["cut"]
     grid = (w["nu_min"], w["dnu"], w["ngrid"])
     nbins, ncheb = w["nbins"], w["ncheb"]
@@ -271,11 +290,7 @@ def run_ours(args):
         stage = ctx.stage_times()
         ctx.set_profiling(False)
         ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        ms_step = sum(ms) / len(ms)
-        if dist:
-            t = torch.tensor([ms_step], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_step = float(t.item())
+        ms_step = max_over_ranks(sum(ms) / len(ms), dist, "cuda")
         voigt_ms, voigt_n = stage["voigt"]
         voigt_s = voigt_ms / max(1, voigt_n) * 1e-3
         peak = FMA_PER_CLK_SM[form] * 2 * nsm * max_mhz * 1e6 / 1e12
@@ -332,11 +347,7 @@ def run_ours(args):
             e2e_step()
             torch.cuda.synchronize()
             tt.append(time.perf_counter() - t1)
-        e2e_s = sum(tt) / len(tt)
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(sum(tt) / len(tt), dist, "cuda")
         e2e = {"value": world * r32["evals"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
@@ -465,6 +476,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_surrogate():
+    """Short fixed run for profilers: train the surrogate briefly (1e6
+    samples x 2 epochs), validate it, and run the core-dominated opacity case
+    with routing twice."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1503_03806_gb300 import helk, synth
+    ctx = helk.Context(0)
+    ctx.surrogate_init(7)
+    ctx.surrogate_train(1_000_000, 11, 2, batch=4096, lr=3e-3)
+    ctx.surrogate_validate(32, 32, 8, 1e-3)
+    ctx.upload(synth.random_lines(3000, 601, 10000.0, 10300.0))
+    k = torch.empty(300_000, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ctx.opacity(1500.0, 0.01, 18.0, ("abs", 0.3), (10000.0, 0.001, 300_000), out=k,
+                    precision=helk.HELK_PREC_F32_KAHAN, surrogate=True)
+    ctx.sync()
+    ctx.close()
+
+
 def run_profile_case(form):
     """Short fixed run for profilers: upload the workload, autotune the Voigt
     tile shape as the benchmark does (3 candidates x 4 launches of the Voigt
@@ -498,10 +530,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tp-grid", action="store_true", help="skip the batched 64-condition leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
-    ap.add_argument("--profile-case", choices=["f32", "f64"], default=None,
+    ap.add_argument("--profile-case", choices=["f32", "f64", "surrogate"], default=None,
                     help="run a short fixed case for ncu and exit")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.profile_case == "surrogate":
+        run_profile_surrogate()
+    elif args.profile_case:
         run_profile_case(args.profile_case)
     elif args.impl == "reference":
         run_reference(args)

@@ -131,8 +131,17 @@ const char *helk_last_error(const helk_ctx *ctx);
 /* Change the stream later work is enqueued on. */
 helk_status helk_set_stream(helk_ctx *ctx, void *stream);
 
-/* Wait for all work of the context and report kernel-side errors. */
+/* Wait for all work of the context and report kernel-side errors (a bounded
+ * wait that gave up: HELK_ERR_TIMEOUT, reported once; the context stays
+ * usable). */
 helk_status helk_sync(helk_ctx *ctx);
+
+/* Failure-detection self-test: launches a kernel whose bounded wait, the
+ * one every staged copy of the Voigt kernels uses, waits on a barrier that
+ * nothing completes; it gives up after `polls` polls (>= 1) and sets the
+ * timeout flag, so the next helk_sync returns HELK_ERR_TIMEOUT.  No fault,
+ * no hang. */
+helk_status helk_selftest_timeout(helk_ctx *ctx, int32_t polls);
 
 /* Upload (copy) a line list into context-owned device memory and order it
  * by nu0 (stable), replacing any previous list.  `on_device` = 0: the

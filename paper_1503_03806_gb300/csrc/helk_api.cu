@@ -179,8 +179,11 @@ helk_status helk_sync(helk_ctx *c) {
   HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "stream synchronize"));
   HELK_TRY(cuda_check(c, cudaMemcpy(c->stats_host, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost),
                       "read status"));
-  if (c->stats_host->err_flags & ERRF_TIMEOUT)
-    return set_err(c, HELK_ERR_TIMEOUT, "a kernel's bounded wait on a bulk copy gave up");
+  if (c->stats_host->err_flags & ERRF_TIMEOUT) {
+    // report once, then clear: the context stays usable
+    HELK_TRY(cuda_check(c, cudaMemset(&c->stats->err_flags, 0, sizeof(int)), "clear status"));
+    return set_err(c, HELK_ERR_TIMEOUT, "a kernel's bounded wait gave up");
+  }
   return HELK_OK;
 }
 
@@ -856,6 +859,13 @@ helk_status helk_surrogate_validate(helk_ctx *c, int32_t nx, int32_t ny, int32_t
     HELK_TRY(cuda_check(c, cudaMemcpy(c->squeue, &q, sizeof q, cudaMemcpyHostToDevice), "mask"));
   }
   return HELK_OK;
+}
+
+helk_status helk_selftest_timeout(helk_ctx *c, int32_t polls) {
+  if (!c || polls < 1) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  HELK_TRY(bind_device(c));
+  return cuda_check(c, launch_selftest_timeout(c, polls), "selftest");
 }
 
 helk_status helk_set_profiling(helk_ctx *c, int32_t on) {

@@ -268,6 +268,7 @@ int voigt_tile_candidates(int precision, int *out, int max);
 // condition k at kappa + k * g.n.
 cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
                          double *kappa, int tile_len, int64_t ntiles);
+cudaError_t launch_selftest_timeout(helk_ctx *c, int polls);
 // k_kdist.cu
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,

@@ -434,6 +434,24 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
+// ------------------------------------------------- failure-detection test --
+// One thread waits, with the same bounded wait as the Voigt kernels, on an
+// mbarrier phase that nothing completes; after `polls` polls it sets the
+// timeout flag and returns.
+__global__ void k_selftest_timeout(DevStats *st, long long polls) {
+  __shared__ __align__(8) unsigned long long mbar;
+  if (threadIdx.x != 0) return;
+  const uint32_t mb = smem_addr(&mbar);
+  mbar_init(mb, 1);
+  fence_mbar_init();
+  mbar_wait_bounded(mb, 0, &st->err_flags, polls);
+}
+
+cudaError_t launch_selftest_timeout(helk_ctx *c, int polls) {
+  k_selftest_timeout<<<1, 32, 0, c->stream>>>(c->stats, polls);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- launch --
 constexpr int F64_BLOCK = 256, F64_PPT = 8, F64_LCH = 64;
 constexpr int F32_BLOCK = 256, F32_LCH = 256;

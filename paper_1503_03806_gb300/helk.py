@@ -73,6 +73,7 @@ SIGNATURES = [
                                           ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts), _P]),
     ("helk_opacity_batch_stats", ctypes.c_int, [_P, _I32, _P, _P]),
     ("helk_transmission", ctypes.c_int, [_P, _I32, _I64, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    ("helk_selftest_timeout", ctypes.c_int, [_P, _I32]),
     ("helk_surrogate_init", ctypes.c_int, [_P, ctypes.c_uint64]),
     ("helk_surrogate_params", ctypes.c_int, [_P, _P, _P]),
     ("helk_surrogate_samples", ctypes.c_int, [_P, _I64, ctypes.c_uint64, _P, _P, _P, _P]),
