@@ -499,8 +499,9 @@ def run_profile_surrogate():
 
 def run_profile_case(form):
     """Short fixed run for profilers: upload the workload, autotune the Voigt
-    tile shape as the benchmark does (3 candidates x 4 launches of the Voigt
-    kernel), then two passes of opacity (FP32 or FP64 form) + k-tables."""
+    tile shape as the benchmark does (4 launches of the Voigt kernel per
+    built tile shape; the count is printed, for ncu's -s), then two passes of
+    opacity (FP32 or FP64 form) + k-tables."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -510,7 +511,9 @@ def run_profile_case(form):
     ctx = helk.Context(0)
     ctx.upload(synth.workload_lines(WORKLOAD))
     grid = (w["nu_min"], w["dnu"], w["ngrid"])
-    ctx.autotune(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], grid, precision=prec)
+    tile = ctx.autotune(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], grid, precision=prec)
+    print("profile case %s: %d autotune launches of the Voigt kernel, then tile %d"
+          % (form, 4 * len(helk.helk_tile_candidates(prec)), tile), flush=True)
     kappa = torch.empty(w["ngrid"], dtype=torch.float64, device="cuda")
     for _ in range(2):
         ctx.opacity(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], (w["nu_min"], w["dnu"], w["ngrid"]),

@@ -226,6 +226,20 @@ helk_status helk_autotune(helk_ctx *ctx, double T, double P_atm,
                           const helk_grid *grid, const helk_opts *opts,
                           int32_t *tile_out);
 
+/* The built Voigt tile shapes of a precision (points per CTA tile,
+ * ascending): writes up to `max` of them to out (host memory) and returns
+ * how many there are.  No device work; returns 0 for an unknown precision
+ * or out == NULL. */
+int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max);
+
+/* Fixes the Voigt tile shape of `precision` for grids of n points (what
+ * helk_autotune would store), or, with tile == 0, returns to the built-in
+ * choice.  tile must be one of helk_tile_candidates(precision); anything
+ * else returns HELK_ERR_INVALID_ARG.  The shape changes no FP64 result and
+ * FP32 results only at rounding level (Kahan-compensated sums in another
+ * grouping). */
+helk_status helk_set_tile(helk_ctx *ctx, int32_t precision, int64_t n, int32_t tile);
+
 /* Stage timing (tracing).  With profiling on, the library records a CUDA
  * event pair on the context stream around each stage it launches:
  *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.5)

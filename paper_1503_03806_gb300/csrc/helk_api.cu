@@ -376,7 +376,7 @@ static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const 
   HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->tile_counter, 0, sizeof(unsigned int), c->stream),
                       "voigt"));
   if (o.surrogate)
-    HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->squeue->count, 0, sizeof(unsigned int), c->stream), "voigt"));
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->squeue->count, 0, sizeof(unsigned long long), c->stream), "voigt"));
   HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
   if (o.surrogate) HELK_TRY(cuda_check(c, launch_mlp_queue(c, n_cond, g->n, o.weight, kappa), "surrogate"));
   return HELK_OK;
@@ -429,8 +429,8 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
   const int prec = o.precision == HELK_PREC_F32_KAHAN ? 1 : 0;
   c->tuned_tile[prec] = 0;  // time the candidates, not the previous choice
-  int cand[8];
-  const int ncand = voigt_tile_candidates(o.precision, cand, 8);
+  int cand[16];
+  const int ncand = voigt_tile_candidates(o.precision, cand, 16);
   int64_t max_tiles = 0;
   for (int i = 0; i < ncand; ++i) max_tiles = std::max(max_tiles, (g->n + cand[i] - 1) / cand[i]);
   HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles));
@@ -479,11 +479,11 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
 static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const helk_cutoff *cut,
                              const helk_grid *g, const helk_opts &o, const double *kappa, int tile) {
   char b[512];
-  snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%p|%d|%p|%p|%p|%p", n_cond,
+  snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%d|%p|%d|%p|%p|%p|%p|%p", n_cond,
            (long long)c->nlines, (const void *)c->nu0, mass, cut->kind, cut->value, cut->cap, g->nu_min,
-           g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions,
+           g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions, o.surrogate,
            (const void *)kappa, tile, (const void *)c->rec64, (const void *)c->rec32,
-           (const void *)c->tile_lo, (const void *)c->cstats);
+           (const void *)c->tile_lo, (const void *)c->cstats, (const void *)c->squeue);
   return std::string(b);
 }
 
@@ -858,6 +858,35 @@ helk_status helk_surrogate_validate(helk_ctx *c, int32_t nx, int32_t ny, int32_t
     q.ny = ny;
     HELK_TRY(cuda_check(c, cudaMemcpy(c->squeue, &q, sizeof q, cudaMemcpyHostToDevice), "mask"));
   }
+  return HELK_OK;
+}
+
+int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max) {
+  if (!out || (precision != HELK_PREC_F64 && precision != HELK_PREC_F32_KAHAN)) return 0;
+  int cand[16];
+  const int n = voigt_tile_candidates(precision, cand, 16);
+  for (int i = 0; i < n && i < max; ++i) out[i] = cand[i];
+  return n;
+}
+
+helk_status helk_set_tile(helk_ctx *c, int32_t precision, int64_t n, int32_t tile) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (precision != HELK_PREC_F64 && precision != HELK_PREC_F32_KAHAN)
+    return set_err(c, HELK_ERR_INVALID_ARG, "set_tile: unknown precision");
+  if (n < 1) return set_err(c, HELK_ERR_INVALID_ARG, "set_tile: n must be >= 1");
+  const int prec = precision == HELK_PREC_F32_KAHAN ? 1 : 0;
+  if (tile == 0) {
+    c->tuned_tile[prec] = 0;
+    return HELK_OK;
+  }
+  int cand[16];
+  const int nc = voigt_tile_candidates(precision, cand, 16);
+  bool ok = false;
+  for (int i = 0; i < nc; ++i) ok = ok || cand[i] == tile;
+  if (!ok) return set_err(c, HELK_ERR_INVALID_ARG, "set_tile: not a built tile shape");
+  c->tuned_tile[prec] = tile;
+  c->tuned_n[prec] = n;
   return HELK_OK;
 }
 

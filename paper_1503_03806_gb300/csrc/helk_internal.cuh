@@ -31,6 +31,7 @@ constexpr double SQRTLN2 = 0.83255461115769775635316;    // sqrt(ln 2)
 constexpr double SQRTLN2PI = 0.46971863934982566688617;  // sqrt(ln 2 / pi)
 constexpr double SQRTPI = 1.7724538509055160272982;
 constexpr double INV_SQRTPI = 0.56418958354775628694808;
+constexpr double ASINH_XCORE = 2.99822295029796973884;  // asinh(10): the surrogate's |x| feature scale
 constexpr double GH3_T = 1.2247448713915890490986;       // sqrt(3/2)
 // Region thresholds on r^2 = a^2 + u^2 (Sec. 2.5)
 constexpr double R2_GH3 = 100.0;
@@ -81,8 +82,8 @@ struct DevStats {
 // kernel appends (grid point, condition, scaled S', x, y); entries past
 // `cap` are evaluated in place by Algorithm 916 instead.
 struct SurrQueue {
-  unsigned int count;
-  unsigned int cap;
+  unsigned long long count;  // 64-bit: a batch call may route more than 2^32 evaluations
+  unsigned long long cap;
   int32_t *idx, *cond;
   float *w, *x, *y;
   const uint32_t *mask;  // validated cells of the network, nx * ny bits

@@ -6,6 +6,14 @@
 // L_j = ln max(k_j, kappa_floor) on g_j = (j + 1/2)/N_b and the least-squares
 // Chebyshev coefficients c = P L, where P is the pseudo-inverse of the design
 // matrix (shared by all bins of one size; computed once by k_pinv).
+//
+// FP64 is the scarce unit of this GPU (1/64 of the FP32 rate), so the two
+// per-point costs that would be FP64 are moved to FP32 where that keeps
+// FP64-level accuracy: ln takes its second-order tail in FP32 (absolute
+// error < 1e-13), and c = P L is a double-float dot product -- P and L are
+// each split into FP32 high and low parts, and every term hi*hi is summed
+// exactly (two-product and two-sum), the cross terms in FP32 (relative
+// error ~2^-46 of the sum of |P_kj L_j|).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -37,9 +45,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // (ACM TOMS 16(4), 1990): x = 2^e m with m in [1, 2), c_j = 1 + j/128 where j
 // is the top 7 fraction bits of m, so f = m - c_j is exact and
 // r = f / c_j lies in [0, 1/128); then ln x = e ln2 + ln c_j + log1p(r) with
-// the Taylor series of log1p to r^7 (truncation < 2^-59 relative to r).  The
-// 128 entries ln c_j, 1/c_j live in shared memory.  Subnormal arguments take
-// the library log.
+// log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6 + r^4/7) (truncation
+// < 2^-59 relative to r).  r and r^2/2 are FP64; the cubic remainder
+// (< 2^-21) is FP32, absolute error < 2^-44.  The 128 entries ln c_j, 1/c_j
+// live in shared memory.  Subnormal arguments take the library log.
 constexpr double LOG_LN2 = 0.69314718055994530941723;
 
 __device__ __forceinline__ double log_table(double x, const double *lnc, const double *invc) {
@@ -50,12 +59,13 @@ __device__ __forceinline__ double log_table(double x, const double *lnc, const d
   const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
   const double cj = __longlong_as_double(0x3FF0000000000000LL | ((long long)j << 45));
   const double r = (m - cj) * invc[j];
-  double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
-  p = fma(p, r, 1.0 / 5.0);
-  p = fma(p, r, -1.0 / 4.0);
-  p = fma(p, r, 1.0 / 3.0);
-  p = fma(p, r, -0.5);
-  p = fma(p, r * r, r);
+  const float rf = (float)r;
+  float q = fmaf(rf, 1.0f / 7.0f, -1.0f / 6.0f);
+  q = fmaf(q, rf, 1.0f / 5.0f);
+  q = fmaf(q, rf, -1.0f / 4.0f);
+  q = fmaf(q, rf, 1.0f / 3.0f);
+  const float cub = (rf * rf) * (rf * q);
+  const double p = fma(-0.5 * r, r, (double)cub) + r;
   return fma((double)(ex - 1023), LOG_LN2, lnc[j] + p);
 }
 
@@ -142,7 +152,7 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
       __syncthreads();
     }
   }
-  // P[:, j] = R^{-1} Q_1[j, :]^T, stored k-major (P[k*nb + j])
+  // P[:, j] = R^{-1} Q_1[j, :]^T, stored k-major (P[k*nb + j]) as split pairs
   for (int64_t j = tid; j < nb; j += PI_THREADS) {
     double p[NCHEB_MAX];
     for (int k = ncheb - 1; k >= 0; --k) {
@@ -150,7 +160,12 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
       for (int m = k + 1; m < ncheb; ++m) v -= R[k * NCHEB_MAX + m] * p[m];
       p[k] = v / R[k * NCHEB_MAX + k];
     }
-    for (int k = 0; k < ncheb; ++k) P[(int64_t)k * nb + j] = p[k];
+    // stored as FP32 (high, low) pairs, high = fl32(P), low = fl32(P - high)
+    float2 *Ps = reinterpret_cast<float2 *>(P);
+    for (int k = 0; k < ncheb; ++k) {
+      const float hi = (float)p[k];
+      Ps[(int64_t)k * nb + j] = make_float2(hi, (float)(p[k] - (double)hi));
+    }
   }
   if (tid == 0 && vtv_out) vtv_out[0] = vtv[0];
 }
@@ -161,14 +176,22 @@ cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
 }
 
 // --------------------------------------------------- block-wide helpers --
-// Exclusive scan of KD_THREADS*8 counters h[0..4095] in place.
+// Per-(digit, warp) counters, digit-major in scan order (position 16 d + w)
+// but stored with row stride 17: the lanes of a warp look up counters of
+// different digits, which stride 16 would put in 2 of the 32 banks.
+constexpr int KD_HIST = 256 * (KD_WARPS + 1);
+static_assert(KD_WARPS == 16, "counter layout assumes 16 warps");
+__device__ __forceinline__ int hidx(uint32_t d, int w) { return (int)d * (KD_WARPS + 1) + w; }
+
+// Exclusive scan of the KD_THREADS*8 counters in scan order, in place.
 __device__ void block_exscan_4096(uint32_t *h, uint32_t *wtot) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   uint32_t loc[8];
   uint32_t s = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    loc[i] = h[tid * 8 + i];
+    const int pos = tid * 8 + i;
+    loc[i] = h[pos + (pos >> 4)];
     s += loc[i];
   }
   uint32_t v = s;
@@ -190,7 +213,8 @@ __device__ void block_exscan_4096(uint32_t *h, uint32_t *wtot) {
   uint32_t run = v - s + (w > 0 ? wtot[w - 1] : 0u);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    h[tid * 8 + i] = run;
+    const int pos = tid * 8 + i;
+    h[pos + (pos >> 4)] = run;
     run += loc[i];
   }
   __syncthreads();
@@ -200,7 +224,7 @@ __device__ void block_exscan_4096(uint32_t *h, uint32_t *wtot) {
 // B is the second buffer.  Digits whose value is the same in every key are
 // skipped.  Returns the buffer holding the result.
 __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned long long *B, int nb,
-                                              uint32_t *hist /*[256][KD_WARPS]*/, uint32_t *wtot,
+                                              uint32_t *hist /* KD_HIST counters */, uint32_t *wtot,
                                               unsigned long long diff) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int per = (nb + KD_WARPS - 1) / KD_WARPS;
@@ -208,13 +232,13 @@ __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned lo
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = pass * 8;
     if (((diff >> shift) & 0xFFull) == 0) continue;
-    for (int i = tid; i < 256 * KD_WARPS; i += KD_THREADS) hist[i] = 0;
+    for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
     __syncthreads();
     for (int e0 = w0; e0 < w1; e0 += 32) {
       const int e = e0 + lane;
       const uint32_t d = e < w1 ? (uint32_t)((A[e] >> shift) & 0xFF) : 256u + lane;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (d < 256 && (peers & lanemask_lt_kd()) == 0) hist[d * KD_WARPS + w] += __popc(peers);
+      if (d < 256 && (peers & lanemask_lt_kd()) == 0) hist[hidx(d, w)] += __popc(peers);
     }
     __syncthreads();
     block_exscan_4096(hist, wtot);
@@ -224,9 +248,9 @@ __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned lo
       const unsigned long long k = valid ? A[e] : 0ull;
       const uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u + lane;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid) B[hist[d * KD_WARPS + w] + __popc(peers & lanemask_lt_kd())] = k;
+      if (valid) B[hist[hidx(d, w)] + __popc(peers & lanemask_lt_kd())] = k;
       __syncwarp();
-      if (valid && (peers & lanemask_lt_kd()) == 0) hist[d * KD_WARPS + w] += __popc(peers);
+      if (valid && (peers & lanemask_lt_kd()) == 0) hist[hidx(d, w)] += __popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -237,34 +261,98 @@ __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned lo
   return A;
 }
 
-// ---------------------------------------------------- per-bin sort + fit --
-template <bool SMEM_KEYS>
+// Register-resident variant for bins of up to KD_REG_MAX points, sorted in
+// place in one shared-memory array: per pass each warp reads its segment's
+// keys once into registers, counts digits and records, per key, its rank
+// among the warp's earlier keys of the same digit; after the block scan the
+// keys go straight to their places (no second read, no read-modify-write).
+constexpr int KD_ITEMS = 24;                                // keys per lane
+constexpr int KD_REG_MAX = KD_ITEMS * 32 * KD_WARPS;        // 12288
+
+__device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist, uint32_t *wtot,
+                                   unsigned long long diff) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (nb + KD_WARPS - 1) / KD_WARPS;
+  const int w0 = w * per, w1 = min(nb, w0 + per);
+  const uint32_t lt = lanemask_lt_kd();
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = pass * 8;
+    if (((diff >> shift) & 0xFFull) == 0) continue;
+    for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
+    __syncthreads();
+    unsigned long long key[KD_ITEMS];
+    uint32_t code[KD_ITEMS];  // digit | (rank among earlier keys of the digit) << 8
+#pragma unroll
+    for (int i = 0; i < KD_ITEMS; ++i) {
+      if (w0 + 32 * i < w1) {  // warp-uniform
+        const int e = w0 + 32 * i + lane;
+        const bool valid = e < w1;
+        key[i] = valid ? A[e] : 0ull;
+        const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFFull) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+          old = hist[hidx(d, w)];
+          hist[hidx(d, w)] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        code[i] = (d & 0xFFu) | ((old + __popc(peers & lt)) << 8);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    block_exscan_4096(hist, wtot);
+#pragma unroll
+    for (int i = 0; i < KD_ITEMS; ++i) {
+      const int e = w0 + 32 * i + lane;
+      if (w0 + 32 * i < w1 && e < w1) A[hist[hidx(code[i] & 0xFFu, w)] + (code[i] >> 8)] = key[i];
+    }
+    __syncthreads();
+  }
+}
+
+// c_k += P_kj L_j in double-float: (sh, sl) holds the running sum; the
+// product of the high parts is exact as p + e (two-product), p joins sh by
+// two-sum, and e, the two-sum error and the cross terms go to sl.
+__device__ __forceinline__ void dfma_acc(float &sh, float &sl, float2 P, float2 L) {
+  const float p = P.x * L.x;
+  const float e = fmaf(P.x, L.x, -p);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl += err + (e + fmaf(P.x, L.y, P.y * L.x));
+}
+
+// Per-bin sort + fit.  MODE 0: keys in shared memory (nb <= KD_REG_MAX,
+// register-resident passes, one array); MODE 1: keys in the global ping-pong
+// buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
+template <int MODE>
 __global__ void __launch_bounds__(KD_THREADS)
     k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
-                const double *__restrict__ pinv, unsigned long long *gA, unsigned long long *gB,
+                const float2 *__restrict__ P, unsigned long long *gA, unsigned long long *gB,
                 double *__restrict__ coef, double *__restrict__ mean, double *__restrict__ kg_out) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ uint32_t hist[256 * KD_WARPS];
+  __shared__ uint32_t hist[KD_HIST];
   __shared__ uint32_t wtot[32];
   __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
   __shared__ double red[KD_WARPS][NCHEB_MAX + 1];
   __shared__ double s_lnc[128], s_invc[128];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t off = (int64_t)blockIdx.x * nb;
-  unsigned long long *A, *B;
-  if (SMEM_KEYS) {
-    A = (unsigned long long *)dsm;
-    B = A + nb;
-  } else {
-    A = gA + off;
-    B = gB + off;
-  }
+  unsigned long long *A = MODE == 0 ? (unsigned long long *)dsm : gA + off;
   unsigned long long vand = ~0ull, vor = 0ull;
   for (int j = tid; j < nb; j += KD_THREADS) {
     const unsigned long long k = (unsigned long long)__double_as_longlong(kappa[off + j]);
     A[j] = k;
     vand &= k;
     vor |= k;
+  }
+  if (tid < 128) {
+    const double cj = 1.0 + tid / 128.0;
+    s_lnc[tid] = log(cj);
+    s_invc[tid] = 1.0 / cj;
   }
   for (int o = 16; o > 0; o >>= 1) {
     vand &= __shfl_down_sync(0xffffffffu, vand, o);
@@ -281,37 +369,47 @@ __global__ void __launch_bounds__(KD_THREADS)
     vand &= red_and[i];
     vor |= red_or[i];
   }
-  const unsigned long long *S = cta_radix_sort(A, B, nb, hist, wtot, vand ^ vor);
-  // sorted values out, c = P L and the bin sum
-  if (tid < 128) {
-    const double cj = 1.0 + tid / 128.0;
-    s_lnc[tid] = log(cj);
-    s_invc[tid] = 1.0 / cj;
+  unsigned long long *S;
+  if (MODE == 0) {
+    cta_radix_sort_reg(A, nb, hist, wtot, vand ^ vor);
+    S = A;
+  } else {
+    S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
   }
-  __syncthreads();
-  double b[NCHEB_MAX];
-#pragma unroll
-  for (int k = 0; k < NCHEB_MAX; ++k) b[k] = 0.0;
+  // sorted values out, the bin sum, and L_j in place as a split pair
   double ksum = 0.0;
+  float2 *Ls = reinterpret_cast<float2 *>(S);
   for (int j = tid; j < nb; j += KD_THREADS) {
     const double kv = __longlong_as_double((long long)S[j]);
     if (kg_out) kg_out[off + j] = kv;
     ksum += kv;
     const double L = log_table(kv > kappa_floor ? kv : kappa_floor, s_lnc, s_invc);
-#pragma unroll
-    for (int k = 0; k < NCHEB_MAX; ++k)
-      if (k < ncheb) b[k] += pinv[(int64_t)k * nb + j] * L;
-  }
-#pragma unroll
-  for (int k = 0; k < NCHEB_MAX; ++k) {
-    if (k < ncheb) {
-      const double v = warp_sum(b[k]);
-      if (lane == 0) red[w][k] = v;
-    }
+    const float hi = (float)L;
+    Ls[j] = make_float2(hi, (float)(L - (double)hi));
   }
   {
     const double v = warp_sum(ksum);
     if (lane == 0) red[w][NCHEB_MAX] = v;
+  }
+  __syncthreads();
+  // c = P L, eight coefficients per sweep over the points
+  for (int k0 = 0; k0 < ncheb; k0 += 8) {
+    float sh[8], sl[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
+    for (int j = tid; j < nb; j += KD_THREADS) {
+      const float2 L = Ls[j];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], P[(int64_t)(k0 + q) * nb + j], L);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (k0 + q < ncheb) {
+        const double v = warp_sum((double)sh[q] + (double)sl[q]);
+        if (lane == 0) red[w][k0 + q] = v;
+      }
+    }
   }
   __syncthreads();
   if (tid < ncheb) {
@@ -327,25 +425,26 @@ __global__ void __launch_bounds__(KD_THREADS)
 }
 
 int64_t kdist_smem_max_points(helk_ctx *c) {
-  // static smem of k_kdist_bin is ~25 KB; keep 1 KB slack
+  // one shared-memory key array (8 B a point) beside ~26 KB of static smem
   const int64_t fixed = 26 * 1024;
-  int64_t avail = (int64_t)c->max_smem_optin - fixed;
-  return avail > 0 ? avail / 16 : 0;
+  const int64_t avail = (int64_t)c->max_smem_optin - fixed;
+  return std::min<int64_t>(KD_REG_MAX, avail > 0 ? avail / 8 : 0);
 }
 
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
                               double kappa_floor, double *coef, double *mean, double *kg_out) {
   const int nb = (int)(n / nbins);
+  const float2 *P = reinterpret_cast<const float2 *>(c->pinv);
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
-    const size_t smem = (size_t)nb * 16;
-    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = (size_t)nb * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_kdist_bin<true><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, c->pinv,
-                                                              nullptr, nullptr, coef, mean, kg_out);
+    k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, nullptr,
+                                                           nullptr, coef, mean, kg_out);
   } else {
-    k_kdist_bin<false><<<nbins, KD_THREADS, 0, c->stream>>>(
-        kappa, nb, ncheb, kappa_floor, c->pinv, c->sort_a, c->sort_b, coef, mean, kg_out);
+    k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, c->sort_a,
+                                                        c->sort_b, coef, mean, kg_out);
   }
   return cudaGetLastError();
 }
@@ -471,7 +570,7 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
   int smem_optin = 0;
   if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return HELK_ERR_CUDA;
-  const size_t smem = (size_t)nb * 16;
+  const size_t smem = (size_t)nb * 8;
   if ((int64_t)smem + 26 * 1024 > smem_optin) return HELK_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double *ptr;
@@ -499,13 +598,14 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
       S.ncheb = ncheb;
     }
   }
-  if (cudaFuncSetAttribute(k_kdist_bin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return HELK_ERR_CUDA;
   }
-  k_kdist_bin<true><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor, ptr, nullptr,
-                                                     nullptr, coeffs, mean, kg_out);
+  k_kdist_bin<0><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor,
+                                                  reinterpret_cast<const float2 *>(ptr), nullptr, nullptr,
+                                                  coeffs, mean, kg_out);
   return cudaGetLastError() == cudaSuccess ? HELK_OK : HELK_ERR_CUDA;
 }
 

@@ -39,7 +39,6 @@ constexpr int OFF_W1 = 0, OFF_B1 = 128, OFF_W2 = 192, OFF_B2 = 4288, OFF_W3 = 43
 constexpr int MLP_NPARAMS = 8577;
 constexpr int WSTRIDE = 72;   // bf16 row stride of staged weights (bank-conflict free)
 constexpr int ASTRIDE = 136;  // bf16 row stride of the staged transposes (128 samples + 8)
-constexpr double ASINH_XCORE = 2.99822295029796973884;  // asinh(10)
 
 static_assert(OFF_B4 + 1 == MLP_NPARAMS, "parameter layout");
 
@@ -75,16 +74,20 @@ __device__ __forceinline__ float dsiluf_(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
-// Features and reference function (FP64 arguments, as the sample generator
-// and the Voigt kernels hold them).
-__device__ __forceinline__ void mlp_features(double x, double y, float &f1, float &f2) {
-  f1 = (float)(2.0 * asinh(fabs(x)) / ASINH_XCORE - 1.0);
-  f2 = (float)(2.0 * (log10(y) + 4.0) / 5.0 - 1.0);
+// Features and reference function, in FP32: the routed evaluations hold
+// x = |u| and y = a as FP32 values, and the network is trained and validated
+// on exactly this arithmetic (its inputs rounded to FP32 first).  1 - e^{-x^2}
+// is taken as -expm1(-x^2) so that it keeps full relative precision at small x.
+constexpr float INV_ASINH_XCORE_F = (float)(1.0 / ASINH_XCORE);
+
+__device__ __forceinline__ void mlp_features(float x, float y, float &f1, float &f2) {
+  f1 = fmaf(2.0f * INV_ASINH_XCORE_F, asinhf(fabsf(x)), -1.0f);
+  f2 = fmaf(0.4f, log10f(y) + 4.0f, -1.0f);
 }
 
-__device__ __forceinline__ double mlp_kref(double x, double y) {
-  const double e = exp(-x * x);
-  return e * erfcx(y) + (1.0 - e) * y / (SQRTPI * (x * x + y * y));
+__device__ __forceinline__ float mlp_kref(float x, float y) {
+  const float x2 = x * x;
+  return expf(-x2) * erfcxf(y) - expm1f(-x2) * y / ((float)SQRTPI * fmaf(y, y, x2));
 }
 
 // --------------------------------------------------- staged parameters --
@@ -207,15 +210,15 @@ __global__ void __launch_bounds__(256) k_mlp_eval(const float *__restrict__ para
        base += (int64_t)gridDim.x * 128) {
     const int64_t s0 = base + g, s1 = base + g + 8;
     float f[2][2];
-    const double x0 = s0 < n ? x[s0] : 0.0, y0 = s0 < n ? y[s0] : 1.0;
-    const double x1 = s1 < n ? x[s1] : 0.0, y1 = s1 < n ? y[s1] : 1.0;
+    const float x0 = s0 < n ? (float)x[s0] : 0.0f, y0 = s0 < n ? (float)y[s0] : 1.0f;
+    const float x1 = s1 < n ? (float)x[s1] : 0.0f, y1 = s1 < n ? (float)y[s1] : 1.0f;
     mlp_features(x0, y0, f[0][0], f[0][1]);
     mlp_features(x1, y1, f[1][0], f[1][1]);
     float z1[8][4], z2[8][4], z3[8][4], o0, o1;
     mlp_forward16(S, f, z1, z2, z3, o0, o1);
     if ((lane & 3) == 0) {
-      if (s0 < n) kout[s0] = mlp_kref(x0, y0) * exp((double)o0);
-      if (s1 < n) kout[s1] = mlp_kref(x1, y1) * exp((double)o1);
+      if (s0 < n) kout[s0] = (double)(mlp_kref(x0, y0) * expf(o0));
+      if (s1 < n) kout[s1] = (double)(mlp_kref(x1, y1) * expf(o1));
     }
   }
 }
@@ -455,12 +458,14 @@ __global__ void k_mlp_samples(int64_t n, uint64_t seed, float *__restrict__ feat
       if (x * x + y * y < 100.0) break;
     }
     while (x * x + y * y >= 100.0) x *= 0.5;  // y < 10, so this ends
+    x = (double)(float)x;  // the network sees FP32 arguments
+    y = (double)(float)y;
     float f1, f2;
-    mlp_features(x, y, f1, f2);
+    mlp_features((float)x, (float)y, f1, f2);
     const double K = k916_f64(x, y, erfcx(y), sig1_of(y));
     feat[2 * i] = f1;
     feat[2 * i + 1] = f2;
-    tgt[i] = (float)log(K / mlp_kref(x, y));
+    tgt[i] = (float)log(K / (double)mlp_kref((float)x, (float)y));
     if (xs) xs[i] = x;
     if (ys) ys[i] = y;
   }
@@ -503,11 +508,11 @@ __global__ void __launch_bounds__(256) k_mlp_validate(const float *__restrict__ 
       const int cx = (int)(cid % nx), cy = (int)(cid / nx);
       const double f1 = -1.0 + 2.0 * (cx + ((sub % per) + 0.5) / per) / nx;
       const double f2 = -1.0 + 2.0 * (cy + ((sub / per) + 0.5) / per) / ny;
-      xs[r] = sinh(0.5 * (f1 + 1.0) * ASINH_XCORE);
-      ys[r] = pow(10.0, 2.5 * (f2 + 1.0) - 4.0);
+      xs[r] = (double)(float)sinh(0.5 * (f1 + 1.0) * ASINH_XCORE);
+      ys[r] = (double)(float)pow(10.0, 2.5 * (f2 + 1.0) - 4.0);
       ok[r] = id < n && xs[r] * xs[r] + ys[r] * ys[r] < 100.0;
       cell[r] = (int)cid;
-      mlp_features(xs[r], ys[r], f[r][0], f[r][1]);
+      mlp_features((float)xs[r], (float)ys[r], f[r][0], f[r][1]);
     }
     float z1[8][4], z2[8][4], z3[8][4], o[2];
     mlp_forward16(S, f, z1, z2, z3, o[0], o[1]);
@@ -515,7 +520,7 @@ __global__ void __launch_bounds__(256) k_mlp_validate(const float *__restrict__ 
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if (!ok[r]) continue;
-        const double kn = mlp_kref(xs[r], ys[r]) * exp((double)o[r]);
+        const double kn = (double)(mlp_kref((float)xs[r], (float)ys[r]) * expf(o[r]));
         const double ke = k916_f64(xs[r], ys[r], erfcx(ys[r]), sig1_of(ys[r]));
         const double e = fabs(kn - ke) / ke;
         atomicMax(&err[cell[r]], (unsigned long long)__double_as_longlong(e));
@@ -532,20 +537,20 @@ __global__ void __launch_bounds__(256) k_mlp_queue(const float *__restrict__ par
                                                    double *__restrict__ kappa) {
   extern __shared__ __align__(16) unsigned char dsm[];
   MlpSmem &S = *reinterpret_cast<MlpSmem *>(dsm);
-  const int64_t n = min(q->count, q->cap);
+  const int64_t n = (int64_t)min(q->count, q->cap);
   if ((int64_t)blockIdx.x * 128 >= n) return;
   stage_params(params, S, false);
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; base < n;
        base += (int64_t)gridDim.x * 128) {
-    double xs[2], ys[2];
+    float xs[2], ys[2];
     float f[2][2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int64_t e = base + g + 8 * r;
-      xs[r] = e < n ? (double)q->x[e] : 0.0;
-      ys[r] = e < n ? (double)q->y[e] : 1.0;
+      xs[r] = e < n ? q->x[e] : 0.0f;
+      ys[r] = e < n ? q->y[e] : 1.0f;
       mlp_features(xs[r], ys[r], f[r][0], f[r][1]);
     }
     float z1[8][4], z2[8][4], z3[8][4], o[2];
@@ -556,7 +561,7 @@ __global__ void __launch_bounds__(256) k_mlp_queue(const float *__restrict__ par
         const int64_t e = base + g + 8 * r;
         if (e >= n) continue;
         const int cond = q->cond[e];
-        const double K = mlp_kref(xs[r], ys[r]) * exp((double)o[r]);
+        const double K = (double)(mlp_kref(xs[r], ys[r]) * expf(o[r]));
         atomicAdd(&kappa[(int64_t)cond * ngrid + q->idx[e]],
                   ldexp(weight * (double)q->w[e] * K, cst[cond].scale_exp));
       }

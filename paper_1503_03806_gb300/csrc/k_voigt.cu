@@ -18,6 +18,7 @@
 //   k_voigt_f32  FP32 profile evaluation on records with strengths scaled by
 //                2^-E, Kahan-compensated FP32 accumulation per point, result
 //                converted to FP64 and rescaled at the flush.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -215,21 +216,37 @@ __global__ void __launch_bounds__(BLOCK)
 // branch-free loop over all slots (independent chains the compiler can
 // interleave); mixed pairs -- those containing a method boundary or the line
 // core -- decide per point.
-enum { CLS_GH1 = 0, CLS_GH3 = 1, CLS_MIXED = 2 };
-constexpr float F32_T1SQ = 1.5f;            // square of the GH3 node sqrt(3/2)
+enum { CLS_GH1 = 1, CLS_GH3 = 2, CLS_MIXED = 3 };  // 0: the line misses the warp
 constexpr int KAHAN_GROUP = 8;              // lines per compensated partial
 
 // Whether a core evaluation at (x, y) lies in a cell where the surrogate
 // network was validated (features as in k_mlp.cu).
-__device__ __forceinline__ bool surr_route(const SurrQueue *sq, float x, float y) {
-  if (!(y >= 1.0e-4f && y < 10.0f)) return false;
-  const float f1 = 2.0f * asinhf(x) * 0.33352f - 1.0f;  // 1/asinh(10)
+// The routing decision is split into a per-line part (the row of validated
+// cells for y = a, or -1 when a is outside the network's range) and a
+// per-point part (the column of x = |u|), both as in the network's features.
+__device__ __forceinline__ int surr_row(const SurrQueue *sq, float y) {
+  if (!sq || !(y >= 1.0e-4f && y < 10.0f)) return -1;
   const float f2 = 0.4f * (log10f(y) + 4.0f) - 1.0f;
-  int cx = (int)((f1 + 1.0f) * 0.5f * sq->nx), cy = (int)((f2 + 1.0f) * 0.5f * sq->ny);
-  cx = min(max(cx, 0), sq->nx - 1);
-  cy = min(max(cy, 0), sq->ny - 1);
-  const int cell = cy * sq->nx + cx;
+  const int cy = min(max((int)((f2 + 1.0f) * 0.5f * sq->ny), 0), sq->ny - 1);
+  return cy * sq->nx;
+}
+
+__device__ __forceinline__ bool surr_route(const SurrQueue *sq, int row, float x) {
+  const float f1 = 2.0f * asinhf(x) * (float)(1.0 / ASINH_XCORE) - 1.0f;
+  const int cx = min(max((int)((f1 + 1.0f) * 0.5f * sq->nx), 0), sq->nx - 1);
+  const int cell = row + cx;
   return (sq->mask[cell >> 5] >> (cell & 31)) & 1u;
+}
+
+// One queue slot per calling lane: the lanes that arrive together take one
+// atomicAdd for all of them (a single counter would otherwise see one atomic
+// per routed evaluation).
+__device__ __forceinline__ unsigned long long surr_reserve(SurrQueue *sq) {
+  namespace cg = cooperative_groups;
+  const cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&sq->count, (unsigned long long)g.size());
+  return g.shfl(base, 0) + g.thread_rank();
 }
 
 // Hardware reciprocal approximation (max relative error ~1 ulp); every
@@ -247,19 +264,36 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
-// 3-node Gauss-Hermite in the form (a w1/pi) [4/r2 + 2q/p] with
-// q = r2 + t^2 and p = d1 d2 = q^2 - 4 t^2 u^2 (no cancellation for r2 >= 100);
-// P3h = Sp a (sqrt(pi)/6)/pi * 2 folded per line.  Returns the term.
-__device__ __forceinline__ float gh3_term(float u, float r2, float P3h) {
-  const float q = r2 + F32_T1SQ;
-  const float m = (u * u) * (-4.0f * F32_T1SQ);
-  const float p = fmaf(q, q, m);
-  const float num = fmaf(2.0f, p, r2 * q);
-  return P3h * (num * fast_rcp(r2 * p));
-}
+// 3-node Gauss-Hermite (nodes 0, +-t, t^2 = 3/2, weights 4 w1, w1):
+//   (a w1/pi) [4/r2 + 2q/p],  q = r2 + t^2,  p = ((u-t)^2+a^2)((u+t)^2+a^2).
+// With u^2 = r2 - a^2 both factors are polynomials in r2 alone:
+//   p = r2 (r2 - 3) + C,  C = 9/4 + 6 a^2,
+//   2p + q r2 = r2 (3 r2 - 9/2) + 2C,
+// so the term is n / (r2 p) with n = r2 (c3 r2 + c45) + c2, the line's
+// factor P3h = 2 a w1 S'/pi folded into c3 = 3 P3h, c45 = -9/2 P3h,
+// c2 = 2C P3h.  No cancellation for r2 >= 100 (r2^2 >= 33 x 3 r2); FP32
+// relative error < 5e-7 over 100 <= r2 < 1e6.
+struct Gh3Line {
+  float a2, C, c3, c45, c2;
+  __device__ __forceinline__ Gh3Line(float a2_, float P3) {
+    const float P3h = 2.0f * P3;
+    a2 = a2_;
+    C = fmaf(6.0f, a2_, 2.25f);
+    c3 = 3.0f * P3h;
+    c45 = -4.5f * P3h;
+    c2 = P3h * fmaf(12.0f, a2_, 4.5f);
+  }
+  // part + term, for the point's r2 = u^2 + a^2
+  __device__ __forceinline__ float add(float part, float r2) const {
+    const float p = fmaf(r2, r2 - 3.0f, C);
+    const float n = fmaf(r2, fmaf(c3, r2, c45), c2);
+    return fmaf(n, fast_rcp(r2 * p), part);
+  }
+};
 
-template <int BLOCK, int NSLOT, int LCH, bool COUNT>
-__global__ void __launch_bounds__(BLOCK)
+// MINB resident CTAs per SM: 3 (<= 85 registers a thread) or 2.
+template <int BLOCK, int NSLOT, int LCH, bool COUNT, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
     k_voigt_f32(const LineRec32 *__restrict__ rec_all, int64_t nlines,
                 const int32_t *__restrict__ tlo_all, const int32_t *__restrict__ thi_all,
                 int64_t ntiles, const int *__restrict__ cond_order, int n_cond, int ngrid,
@@ -273,7 +307,9 @@ __global__ void __launch_bounds__(BLOCK)
   constexpr int WSPAN = 32 * NSLOT;
   __shared__ __align__(128) LineRec32 sl[2][LCH];
   __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t s_cls[LCH];
   __shared__ int s_item;
+  static_assert(BLOCK / 32 * 3 <= 32, "3 class bits per warp");
   const int lane = threadIdx.x & 31;
   LineStager<LineRec32, LCH> stg;
   stg.init(sl, mbar);
@@ -302,10 +338,38 @@ __global__ void __launch_bounds__(BLOCK)
     if (!stg.acquire(ch, &st->err_flags)) return;
     const int cnum = stg.count(ch);
     const LineRec32 *buf = stg.buffer(ch);
-    for (int j = 0; j < cnum; ++j) {
+    // Method class of every (line, warp) pair of the chunk, one thread per
+    // line: 3 bits per warp (class, and whether the line covers the warp's
+    // whole span).  The extreme r^2 over the warp's covered points [lo, hi]
+    // decides it: r^2(d) is monotone on each side of the line centre in the
+    // FP32 arithmetic of the evaluation loops.
+    for (int j = threadIdx.x; j < cnum; j += BLOCK) {
       const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
-      const int lo = max(ilo, wbase), hi = min(ihi, wbase + WSPAN - 1);
-      if (lo > hi) continue;  // warp-uniform
+      const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
+      uint32_t code = 0;
+#pragma unroll
+      for (int w = 0; w < BLOCK / 32; ++w) {
+        const int wb = base + w * WSPAN;
+        const int lo = max(ilo, wb), hi = min(ihi, wb + WSPAN - 1);
+        if (lo > hi) continue;
+        const int dlo = lo - c, dhi = hi - c;
+        const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
+        const float un = fmaf((float)dnear, beta, nphi);
+        const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
+        const float r2near = fmaf(un, un, a2);
+        const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
+        const uint32_t cls = r2near >= 1.0e6f ? CLS_GH1
+                                              : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
+        const uint32_t full = (lo == wb) && (hi == wb + WSPAN - 1);
+        code |= (cls | (full << 2)) << (3 * w);
+      }
+      s_cls[j] = code;
+    }
+    __syncthreads();
+    const int wshift = 3 * (threadIdx.x >> 5);
+    for (int j = 0; j < cnum; ++j) {
+      const uint32_t code = (s_cls[j] >> wshift) & 7u;
+      if (code == 0) continue;  // warp-uniform: the line misses this warp
       if (++ngroup == KAHAN_GROUP) {
         ngroup = 0;
 #pragma unroll
@@ -314,17 +378,11 @@ __global__ void __launch_bounds__(BLOCK)
           part[k] = 0.0f;
         }
       }
+      const int cls = (int)(code & 3u);
+      const bool full = (code & 4u) != 0;
+      const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
+      const int lo = max(ilo, wbase), hi = min(ihi, wbase + WSPAN - 1);
       const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
-      // extreme r^2 over the warp's covered points [lo, hi]
-      const int dlo = lo - c, dhi = hi - c;
-      const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
-      const float un = fmaf((float)dnear, beta, nphi);
-      const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
-      const float r2near = fmaf(un, un, a2);
-      const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
-      const int cls = r2near >= 1.0e6f ? CLS_GH1
-                                       : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
-      const bool full = (lo == wbase) && (hi == wbase + WSPAN - 1);
       // (i - c) of this lane's first point, exact in FP32
       const float d0 = (float)(wbase + lane - c);
       if (cls == CLS_GH1) {
@@ -349,13 +407,12 @@ __global__ void __launch_bounds__(BLOCK)
           }
         }
       } else if (cls == CLS_GH3) {
-        const float P3h = 2.0f * buf[j].P3;
+        const Gh3Line g3(a2, buf[j].P3);
         if (full) {
 #pragma unroll
           for (int k = 0; k < NSLOT; ++k) {
             const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-            const float r2 = fmaf(u, u, a2);
-            part[k] += gh3_term(u, r2, P3h);
+            part[k] = g3.add(part[k], fmaf(u, u, a2));
           }
           if (COUNT) cnt[1] += NSLOT;
         } else {
@@ -365,41 +422,42 @@ __global__ void __launch_bounds__(BLOCK)
             const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
             const float r2 = fmaf(u, u, a2);
             const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
-            part[k] += in ? gh3_term(u, r2, P3h) : 0.0f;
+            part[k] = in ? g3.add(part[k], r2) : part[k];
             if (COUNT) cnt[1] += in;
           }
         }
       } else {
-        const float P1 = buf[j].P1, P3h = 2.0f * buf[j].P3;
+        // Per point: GH1, GH3 or, in the core, Algorithm 916 (or the
+        // surrogate's queue when routed).
+        const float P1 = buf[j].P1;
+        const Gh3Line g3(a2, buf[j].P3);
+        const int srow = surr_row(sq, buf[j].a);
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
           const int i = wbase + lane + 32 * k;
           if ((unsigned)(i - lo) <= (unsigned)(hi - lo)) {
             const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
             const float r2 = fmaf(u, u, a2);
-            float v;
             if (r2 >= 1.0e6f) {
-              v = P1 * fast_rcp(r2);
+              part[k] = fmaf(P1, fast_rcp(r2), part[k]);
               if (COUNT) cnt[2]++;
             } else if (r2 >= 100.0f) {
-              v = gh3_term(u, r2, P3h);
+              part[k] = g3.add(part[k], r2);
               if (COUNT) cnt[1]++;
             } else {
-              if (sq && surr_route(sq, fabsf(u), buf[j].a)) {
-                const unsigned slot = atomicAdd(&sq->count, 1u);
+              bool routed = false;
+              if (srow >= 0 && surr_route(sq, srow, fabsf(u))) {
+                const unsigned long long slot = surr_reserve(sq);
                 if (slot < sq->cap) {
                   sq->idx[slot] = i;
                   sq->cond[slot] = cond;
                   sq->w[slot] = buf[j].Sp;
                   sq->x[slot] = fabsf(u);
                   sq->y[slot] = buf[j].a;
-                  v = 0.0f;
-                } else {
-                  v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+                  routed = true;
                 }
-              } else {
-                v = buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
               }
+              if (!routed) part[k] += buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
               if (COUNT) {
                 int n0, n1;
                 a916_range(fabs((double)u), n0, n1);
@@ -407,7 +465,6 @@ __global__ void __launch_bounds__(BLOCK)
                 cnt[3] += (unsigned long long)(n1 - n0 + 1);
               }
             }
-            part[k] += v;
           }
         }
       }
@@ -489,19 +546,22 @@ static int pick_nslot(int64_t n, int block, int ppt, int slots) {
 }
 
 // FP32 tiles: NSLOT is a template parameter (no per-slot bounds test in the
-// hot loops); the instantiated choices are 8, 12 and 16 slots.
-#define HELK_F32_NSLOTS(X) X(8) X(12) X(16)
+// hot loops).  The tile is 256 NSLOT points; the choices span 6..16 slots so
+// that the number of tiles can be matched to whole waves of resident CTAs
+// (equal tiles finish together, so a partial last wave idles the rest of the
+// GPU).  X(NSLOT, resident CTAs per SM the kernel is compiled for).
+#define HELK_F32_NSLOTS(X) X(6, 3) X(7, 3) X(8, 3) X(9, 3) X(10, 3) X(11, 3) X(12, 3) X(13, 3) X(14, 3) X(16, 2)
+constexpr int F32_COUNT_NSLOT = 8;  // the counting variant (statistics) uses one tile shape
 
-template <int NS>
-static int f32_slots(helk_ctx *c, bool count) {
-  return count ? resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, true>, F32_BLOCK)
-               : resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, false>, F32_BLOCK);
+template <int NS, int MB>
+static int f32_slots(helk_ctx *c) {
+  return resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, false, MB>, F32_BLOCK);
 }
 
 int voigt_tile_candidates(int precision, int *out, int max) {
   int n = 0;
   if (precision == HELK_PREC_F32_KAHAN) {
-#define X(NS) \
+#define X(NS, MB) \
     if (n < max) out[n++] = F32_BLOCK * NS;
     HELK_F32_NSLOTS(X)
 #undef X
@@ -513,19 +573,29 @@ int voigt_tile_candidates(int precision, int *out, int max) {
   return n;
 }
 
+// Wave efficiency of ceil(n / (block p)) equal tiles on `slots` resident
+// CTAs, times the share of a (line, warp) pair's work that is evaluation
+// (the pair's fixed cost is about `setup` slots).
+static double f32_tile_score(int64_t n, int p, int slots) {
+  const int64_t ntiles = (n + (int64_t)F32_BLOCK * p - 1) / ((int64_t)F32_BLOCK * p);
+  const double waves = (double)ntiles / slots;
+  return waves / ceil(waves) * p / (p + 2.5);
+}
+
 int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n) {
   const int prec = precision == HELK_PREC_F32_KAHAN ? 1 : 0;
   if (!count && c->tuned_tile[prec] > 0 && c->tuned_n[prec] == n) return c->tuned_tile[prec];
   if (precision == HELK_PREC_F32_KAHAN) {
-    int best = 16;
+    if (count) return F32_BLOCK * F32_COUNT_NSLOT;
+    int best = 8;
     double best_score = -1.0;
-#define X(NS)                                                        \
-    {                                                                \
-      const double sc = tile_score(n, F32_BLOCK, NS, f32_slots<NS>(c, count)); \
-      if (sc > best_score + 1e-9) {                                  \
-        best_score = sc;                                             \
-        best = NS;                                                   \
-      }                                                              \
+#define X(NS, MB)                                                 \
+    {                                                             \
+      const double sc = f32_tile_score(n, NS, f32_slots<NS, MB>(c)); \
+      if (sc > best_score + 1e-9) {                               \
+        best_score = sc;                                          \
+        best = NS;                                                \
+      }                                                           \
     }
     HELK_F32_NSLOTS(X)
 #undef X
@@ -548,20 +618,21 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
   if (o.precision == HELK_PREC_F32_KAHAN) {
     SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
     const int ns = tile_len / F32_BLOCK;
-#define X(NS)                                                                                   \
-    if (ns == NS) {                                                                             \
-      if (o.count_regions) {                                                                    \
-        auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, true>;                                   \
-        kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
-            c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
-            o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                             \
-      } else {                                                                                  \
-        auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false>;                                  \
-        kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(          \
-            c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, \
-            o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                             \
-      }                                                                                         \
-      return cudaGetLastError();                                                                \
+    if (o.count_regions) {
+      if (ns != F32_COUNT_NSLOT) return cudaErrorInvalidValue;
+      auto kern = k_voigt_f32<F32_BLOCK, F32_COUNT_NSLOT, F32_LCH, true, 3>;
+      kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(
+          c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, o.weight,
+          o.accumulate, kappa, c->cstats, c->stats, sq);
+      return cudaGetLastError();
+    }
+#define X(NS, MB)                                                                                 \
+    if (ns == NS) {                                                                               \
+      auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false, MB>;                                  \
+      kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(              \
+          c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n,    \
+          o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                                 \
+      return cudaGetLastError();                                                                  \
     }
     HELK_F32_NSLOTS(X)
 #undef X

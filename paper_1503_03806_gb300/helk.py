@@ -84,6 +84,8 @@ SIGNATURES = [
     ("helk_autotune", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(helk_cutoff),
                                      ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
                                      ctypes.POINTER(_I32)]),
+    ("helk_tile_candidates", _I32, [_I32, _P, _I32]),
+    ("helk_set_tile", ctypes.c_int, [_P, _I32, _I64, _I32]),
 ]
 HELK_NSTAGES = 4
 MLP_NPARAMS = 8577
@@ -180,6 +182,13 @@ def helk_stage_times(ctx):
 
 
 # -------------------------------------------------------------- Context --
+def helk_tile_candidates(precision):
+    """The built Voigt tile shapes (points per CTA tile) of a precision."""
+    out = (_I32 * 32)()
+    n = lib.helk_tile_candidates(int(precision), out, 32)
+    return [int(out[i]) for i in range(min(n, 32))]
+
+
 def _cut(cut):
     """cut: ("abs", C) | ("lorentz", multiple, cap) | ("none",)"""
     kind = cut[0]
@@ -321,6 +330,10 @@ class Context:
         _check(self.h, lib.helk_autotune(self.h, float(T), float(P), float(mass), ctypes.byref(_cut(cut)),
                                          ctypes.byref(g), ctypes.byref(o), ctypes.byref(t)))
         return int(t.value)
+
+    def set_tile(self, precision, n, tile):
+        """Fix the Voigt tile shape for grids of n points (0: built-in choice)."""
+        _check(self.h, lib.helk_set_tile(self.h, int(precision), int(n), int(tile)))
 
     # ------------------------------------------------------ surrogate --
     def surrogate_init(self, seed=0):
