@@ -270,12 +270,12 @@ constexpr int KD_ITEMS = 24;                                // keys per lane
 constexpr int KD_REG_MAX = KD_ITEMS * 32 * KD_WARPS;        // 12288
 
 __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist, uint32_t *wtot,
-                                   unsigned long long diff) {
+                                   unsigned long long diff, int first_pass) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int per = (nb + KD_WARPS - 1) / KD_WARPS;
   const int w0 = w * per, w1 = min(nb, w0 + per);
   const uint32_t lt = lanemask_lt_kd();
-  for (int pass = 0; pass < 8; ++pass) {
+  for (int pass = first_pass; pass < 8; ++pass) {
     const int shift = pass * 8;
     if (((diff >> shift) & 0xFFull) == 0) continue;
     for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
@@ -310,6 +310,54 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
     }
     __syncthreads();
   }
+}
+
+// Sort by the high 32 bits (sign, exponent, top 20 fraction bits) first: 4
+// passes instead of 8.  Keys that share their high word then sit together in
+// their input order; runs of such ties are put in order by one thread each
+// (insertion sort, runs of up to KD_RUN_MAX keys).  Ties are rare and short
+// (relative differences below 2^-20); runs that are long and out of order
+// make the CTA sort the reloaded keys by all 8 bytes instead.  Returns
+// through `A` the keys in ascending order.
+constexpr int KD_RUN_MAX = 64;
+
+__device__ void cta_sort_bin(unsigned long long *A, const double *__restrict__ src, int nb, uint32_t *hist,
+                             uint32_t *wtot, unsigned long long diff) {
+  const int tid = threadIdx.x;
+  cta_radix_sort_reg(A, nb, hist, wtot, diff, 4);
+  // adjacent keys with equal high words in the wrong order?
+  bool bad = false;
+  for (int j = tid + 1; j < nb; j += KD_THREADS) {
+    const unsigned long long a = A[j - 1], b = A[j];
+    bad |= (a >> 32) == (b >> 32) && b < a;
+  }
+  if (!__syncthreads_or(bad)) return;
+  bool too_long = false;
+  for (int j = tid; j < nb; j += KD_THREADS) {
+    const uint32_t h = (uint32_t)(A[j] >> 32);
+    const bool start = (j == 0 || (uint32_t)(A[j - 1] >> 32) != h) && j + 1 < nb &&
+                       (uint32_t)(A[j + 1] >> 32) == h;
+    if (!start) continue;
+    int e = j + 1;
+    while (e < nb && e - j <= KD_RUN_MAX && (uint32_t)(A[e] >> 32) == h) ++e;
+    if (e - j > KD_RUN_MAX) {
+      too_long = true;
+      continue;
+    }
+    for (int q = j + 1; q < e; ++q) {  // insertion sort of the run
+      const unsigned long long v = A[q];
+      int r = q - 1;
+      while (r >= j && A[r] > v) {
+        A[r + 1] = A[r];
+        --r;
+      }
+      A[r + 1] = v;
+    }
+  }
+  if (!__syncthreads_or(too_long)) return;
+  for (int j = tid; j < nb; j += KD_THREADS) A[j] = (unsigned long long)__double_as_longlong(src[j]);
+  __syncthreads();
+  cta_radix_sort_reg(A, nb, hist, wtot, diff, 0);
 }
 
 // c_k += P_kj L_j in double-float: (sh, sl) holds the running sum; the
@@ -371,7 +419,7 @@ __global__ void __launch_bounds__(KD_THREADS)
   }
   unsigned long long *S;
   if (MODE == 0) {
-    cta_radix_sort_reg(A, nb, hist, wtot, vand ^ vor);
+    cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
     S = A;
   } else {
     S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);

@@ -291,6 +291,83 @@ struct Gh3Line {
   }
 };
 
+// ---- FP32 line pipeline: a ring of F32_STAGES chunks of candidate lines,
+// filled by 1-D bulk copies that complete on the stage's mbarrier, with no
+// CTA-wide barrier in the main loop.  Every warp consumes the chunk stream in
+// order; the warp that finishes a chunk last (a shared-memory counter per
+// stage) refills that stage with the chunk F32_STAGES further on, fetching
+// the next (condition, tile) item from the global counter when the current
+// one has no lines left.  So warps may drift apart by several chunks instead
+// of meeting at a barrier after each one.  Each chunk carries a header (item,
+// first line, count); an item without lines gets one empty chunk so that its
+// tile is still written, and an exhausted item counter ends the stream with
+// an empty chunk of item -1.
+constexpr int F32_STAGES = 6;
+
+struct ChunkHdr {
+  int item, l0, cnt, pad;
+};
+
+struct F32Pipe {
+  ChunkHdr hdr[F32_STAGES];
+  unsigned long long full[F32_STAGES];
+  int done[F32_STAGES];
+  int pending[F32_STAGES];  // parity + 1 of a copy in flight into the stage, else 0
+  int item, pos, end, exhausted;  // the issuer's place in the stream
+};
+
+// Publishes chunk `seq` of the stream into stage seq % F32_STAGES.  Called by
+// one thread at a time (the initial fill, then the last consumer of the chunk
+// that used the stage before).
+template <int LCH>
+__device__ void f32_issue(F32Pipe &P, LineRec32 (*sl)[LCH], unsigned long long seq, const LineRec32 *rec_all,
+                          int64_t nlines, const int32_t *tlo_all, const int32_t *thi_all, int64_t ntiles,
+                          const int *cond_order, int nitems, DevStats *st) {
+  const int s = (int)(seq % F32_STAGES);
+  const uint32_t mb = smem_addr(&P.full[s]);
+  if (P.item < 0 || P.pos >= P.end) {  // the current item has no lines left: take the next one
+    int item = -1;
+    if (!P.exhausted) {
+      item = (int)atomicAdd(&st->tile_counter, 1u);
+      if (item >= nitems) item = -1;
+    }
+    if (item < 0) {
+      P.exhausted = 1;
+      P.hdr[s] = ChunkHdr{-1, 0, 0, 0};
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+      return;
+    }
+    const int cond = cond_order[item / ntiles];
+    const int64_t t = (int64_t)cond * ntiles + item % ntiles;
+    P.item = item;
+    P.pos = tlo_all[t];
+    P.end = thi_all[t];
+    if (P.pos >= P.end) {
+      P.hdr[s] = ChunkHdr{item, P.pos, 0, 0};
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+      return;
+    }
+  }
+  const int cnt = min(LCH, P.end - P.pos);
+  const int cond = cond_order[P.item / ntiles];
+  P.hdr[s] = ChunkHdr{P.item, P.pos, cnt, 0};
+  P.pending[s] = (int)((seq / F32_STAGES) & 1ull) + 1;
+  // the stage's previous contents were read through the generic proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tma_load_1d(smem_addr(&sl[s][0]), rec_all + (int64_t)cond * nlines + P.pos,
+              (uint32_t)(cnt * sizeof(LineRec32)), mb);
+  P.pos += cnt;
+}
+
+// After a failed wait: wait (bounded) for the copies still in flight, so that
+// none lands in shared memory after the CTA has left.
+__device__ void f32_drain(F32Pipe &P, int *flags) {
+  for (int s = 0; s < F32_STAGES; ++s) {
+    const int pend = *((volatile int *)&P.pending[s]);
+    if (pend) mbar_wait_bounded(smem_addr(&P.full[s]), (uint32_t)(pend - 1), flags, WAIT_LIMIT);
+  }
+}
+
 // MINB resident CTAs per SM: 3 (<= 85 registers a thread) or 2.
 template <int BLOCK, int NSLOT, int LCH, bool COUNT, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB)
@@ -303,72 +380,126 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   // base + w WSPAN; lane l holds points base + w WSPAN + 32 k + l.  Method
   // classes are decided per (line, warp), so only the warps whose span holds
   // a method boundary or the line core take the per-point path.
+  constexpr int NW = BLOCK / 32;
   constexpr int TILE = BLOCK * NSLOT;
   constexpr int WSPAN = 32 * NSLOT;
-  __shared__ __align__(128) LineRec32 sl[2][LCH];
-  __shared__ __align__(8) unsigned long long mbar[2];
-  __shared__ uint32_t s_cls[LCH];
-  __shared__ int s_item;
-  static_assert(BLOCK / 32 * 3 <= 32, "3 class bits per warp");
+  constexpr int LPL = LCH / 32;  // lines of a chunk per lane in the class pass
+  static_assert(LCH % 32 == 0 && LPL * 3 <= 32, "3 class bits per line in one word");
+  __shared__ __align__(128) LineRec32 sl[F32_STAGES][LCH];
+  __shared__ __align__(8) F32Pipe P;
   const int lane = threadIdx.x & 31;
-  LineStager<LineRec32, LCH> stg;
-  stg.init(sl, mbar);
   const int nitems = (int)(ntiles * n_cond);
-  for (int item = next_item(st, nitems, &s_item); item >= 0; item = next_item(st, nitems, &s_item)) {
-  const int cond = cond_order[item / ntiles];
-  const int64_t tile = item % ntiles;
-  const LineRec32 *rec = rec_all + cond * nlines;
-  double *kappa = kappa_all + (int64_t)cond * ngrid;
-  const int base = (int)(tile * TILE);
-  const int wbase = base + (threadIdx.x >> 5) * WSPAN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < F32_STAGES; ++s) {
+      mbar_init(smem_addr(&P.full[s]), 1);
+      P.done[s] = 0;
+      P.pending[s] = 0;
+    }
+    P.item = -1;
+    P.pos = P.end = 0;
+    P.exhausted = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (unsigned long long q = 0; q < F32_STAGES; ++q)
+      f32_issue<LCH>(P, sl, q, rec_all, nlines, tlo_all, thi_all, ntiles, cond_order, nitems, st);
+
+  // cur: the item being accumulated; -2 before the first chunk (-1 marks the
+  // end of the stream, so a CTA that gets no item at all still sees a change)
+  int cur = -2, cond = 0, wbase = 0;
+  // No stream is longer than every item's chunks plus the end markers: a
+  // longer one means a logic error, reported instead of looping.
+  const unsigned long long max_seq =
+      (unsigned long long)nitems * (unsigned long long)(nlines / LCH + 2) + 2 * F32_STAGES;
+  double *kappa = nullptr;
   // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
   // into part[k] (relative error <= 7 u) and Kahan-adds the partial into
   // (sum, comp); total relative error < 6e-7.
   float sum[NSLOT], comp[NSLOT], part[NSLOT];
-#pragma unroll
-  for (int k = 0; k < NSLOT; ++k) {
-    sum[k] = 0.0f;
-    comp[k] = 0.0f;
-    part[k] = 0.0f;
-  }
   int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  stg.begin(rec, tlo_all[cond * ntiles + tile], thi_all[cond * ntiles + tile]);
-  for (int ch = 0; ch < stg.nch; ++ch) {
-    if (!stg.acquire(ch, &st->err_flags)) return;
-    const int cnum = stg.count(ch);
-    const LineRec32 *buf = stg.buffer(ch);
-    // Method class of every (line, warp) pair of the chunk, one thread per
-    // line: 3 bits per warp (class, and whether the line covers the warp's
-    // whole span).  The extreme r^2 over the warp's covered points [lo, hi]
-    // decides it: r^2(d) is monotone on each side of the line centre in the
-    // FP32 arithmetic of the evaluation loops.
-    for (int j = threadIdx.x; j < cnum; j += BLOCK) {
-      const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
-      const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
-      uint32_t code = 0;
-#pragma unroll
-      for (int w = 0; w < BLOCK / 32; ++w) {
-        const int wb = base + w * WSPAN;
-        const int lo = max(ilo, wb), hi = min(ihi, wb + WSPAN - 1);
-        if (lo > hi) continue;
-        const int dlo = lo - c, dhi = hi - c;
-        const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
-        const float un = fmaf((float)dnear, beta, nphi);
-        const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
-        const float r2near = fmaf(un, un, a2);
-        const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
-        const uint32_t cls = r2near >= 1.0e6f ? CLS_GH1
-                                              : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
-        const uint32_t full = (lo == wb) && (hi == wb + WSPAN - 1);
-        code |= (cls | (full << 2)) << (3 * w);
+  for (unsigned long long seq = 0;; ++seq) {
+    const int s = (int)(seq % F32_STAGES);
+    if (seq > max_seq) {
+      if (lane == 0) {
+        atomicOr(&st->err_flags, ERRF_TIMEOUT);
+        f32_drain(P, &st->err_flags);
       }
-      s_cls[j] = code;
+      return;
     }
-    __syncthreads();
-    const int wshift = 3 * (threadIdx.x >> 5);
+    if (!mbar_wait_bounded(smem_addr(&P.full[s]), (uint32_t)((seq / F32_STAGES) & 1u), &st->err_flags,
+                           WAIT_LIMIT)) {
+      if (lane == 0) f32_drain(P, &st->err_flags);
+      return;
+    }
+    const ChunkHdr h = P.hdr[s];
+    if (h.item != cur) {
+      if (cur >= 0) {  // the previous tile is complete: write it
+        const double scale = ldexp(weight, cst[cond].scale_exp);
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+          kahan_add(sum[k], comp[k], part[k]);
+          const int i = wbase + lane + 32 * k;
+          if (i < ngrid) {
+            const double v = scale * ((double)sum[k] - (double)comp[k]);
+            kappa[i] = accumulate ? kappa[i] + v : v;
+          }
+        }
+        if (COUNT) {
+          for (int r = 0; r < 4; ++r) {
+            unsigned long long v = cnt[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicAdd(&cst[cond].region[r], v);
+            cnt[r] = 0;
+          }
+        }
+      }
+      if (h.item < 0) return;  // end of the stream
+      cur = h.item;
+      cond = cond_order[cur / ntiles];
+      kappa = kappa_all + (int64_t)cond * ngrid;
+      wbase = (int)((cur % ntiles) * TILE) + (threadIdx.x >> 5) * WSPAN;
+#pragma unroll
+      for (int k = 0; k < NSLOT; ++k) {
+        sum[k] = 0.0f;
+        comp[k] = 0.0f;
+        part[k] = 0.0f;
+      }
+      ngroup = 0;
+    }
+    if (lane == 0) P.pending[s] = 0;
+    const LineRec32 *buf = sl[s];
+    const int cnum = h.cnt;
+    // Method class of (line j, this warp) for the chunk's lines, lane l
+    // taking lines l, l + 32, ...: 3 bits (class, and whether the line covers
+    // the warp's whole span).  The extreme r^2 over the warp's covered points
+    // [lo, hi] decides it: r^2(d) is monotone on each side of the line centre
+    // in the FP32 arithmetic of the evaluation loops.
+    uint32_t mycls = 0;
+#pragma unroll
+    for (int m = 0; m < LPL; ++m) {
+      const int j = lane + 32 * m;
+      if (j < cnum) {
+        const int c = buf[j].c;
+        const int lo = max(buf[j].ilo, wbase), hi = min(buf[j].ihi, wbase + WSPAN - 1);
+        if (lo <= hi) {
+          const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
+          const int dlo = lo - c, dhi = hi - c;
+          const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
+          const float un = fmaf((float)dnear, beta, nphi);
+          const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
+          const float r2near = fmaf(un, un, a2);
+          const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
+          const uint32_t cls = r2near >= 1.0e6f ? CLS_GH1
+                                                : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
+          const uint32_t full = (lo == wbase) && (hi == wbase + WSPAN - 1);
+          mycls |= (cls | (full << 2)) << (3 * m);
+        }
+      }
+    }
     for (int j = 0; j < cnum; ++j) {
-      const uint32_t code = (s_cls[j] >> wshift) & 7u;
+      const uint32_t code = (__shfl_sync(0xffffffffu, mycls, j & 31) >> (3 * (j >> 5))) & 7u;
       if (code == 0) continue;  // warp-uniform: the line misses this warp
       if (++ngroup == KAHAN_GROUP) {
         ngroup = 0;
@@ -469,25 +600,17 @@ __global__ void __launch_bounds__(BLOCK, MINB)
         }
       }
     }
-    __syncthreads();
-  }
-  const double scale = ldexp(weight, cst[cond].scale_exp);
-#pragma unroll
-  for (int k = 0; k < NSLOT; ++k) {
-    kahan_add(sum[k], comp[k], part[k]);
-    const int i = wbase + lane + 32 * k;
-    if (i < ngrid) {
-      const double v = scale * ((double)sum[k] - (double)comp[k]);
-      kappa[i] = accumulate ? kappa[i] + v : v;
+    // release the stage; the last warp out refills it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&P.done[s], 1) == NW - 1) {
+        P.done[s] = 0;
+        __threadfence_block();
+        f32_issue<LCH>(P, sl, seq + F32_STAGES, rec_all, nlines, tlo_all, thi_all, ntiles, cond_order, nitems,
+                       st);
+      }
     }
-  }
-  if (COUNT) {
-    for (int r = 0; r < 4; ++r) {
-      unsigned long long v = cnt[r];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0 && v) atomicAdd(&cst[cond].region[r], v);
-    }
-  }
   }
 }
 
@@ -511,7 +634,7 @@ cudaError_t launch_selftest_timeout(helk_ctx *c, int polls) {
 
 // --------------------------------------------------------------- launch --
 constexpr int F64_BLOCK = 256, F64_PPT = 8, F64_LCH = 64;
-constexpr int F32_BLOCK = 256, F32_LCH = 256;
+constexpr int F32_BLOCK = 256, F32_LCH = 128;
 
 template <typename K>
 static int resident_ctas(helk_ctx *c, K kern, int block) {

@@ -73,6 +73,35 @@ def test_ties_zeros_and_floor(ctx):
     check_kdist(ctx, k, 4, 20, floor=1e-40)
 
 
+def _tied_high_words(n, group, seed):
+    """Opacities in groups of `group` values that share the high 32 bits
+    (sign, exponent, top 20 fraction bits) and differ in the low 32, in
+    random order: the order inside each group is decided by the low word."""
+    rng = np.random.default_rng(seed)
+    base = synth.uniform_kappa(n // group + 1, seed).view(np.uint64) & np.uint64(0xFFFFFFFF00000000)
+    hi = np.repeat(base, group)[:n]
+    lo = rng.integers(0, 2**32, n, dtype=np.uint64)
+    bits = hi | lo
+    rng.shuffle(bits)
+    return bits.view(np.float64)
+
+
+def test_high_word_ties_short_runs(ctx):
+    # runs of 2..5 keys equal in the high word: sorted by the low word after
+    # the high-word passes
+    for group in (2, 3, 5):
+        check_kdist(ctx, _tied_high_words(4 * 9000, group, 20 + group), 4, 20)
+
+
+def test_high_word_ties_long_runs(ctx):
+    # runs longer than one thread sorts (and a long run of zeros beside an
+    # unsorted short one): the bin is sorted again by all eight bytes
+    check_kdist(ctx, _tied_high_words(3 * 8000, 200, 31), 3, 20)
+    k = _tied_high_words(2 * 6000, 2, 32)
+    k[:2000] = 0.0
+    check_kdist(ctx, k, 2, 20, floor=1e-40)
+
+
 def test_constant_bin_skips_all_passes(ctx):
     k = np.full(3 * 777, 3.5e-21)
     check_kdist(ctx, k, 3, 8)
