@@ -264,6 +264,18 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
+// Kahan-adds the group's partials into (sum, comp) and restarts the group.
+template <int NSLOT>
+__device__ __forceinline__ void kahan_flush(int &ngroup, float (&sum)[NSLOT], float (&comp)[NSLOT],
+                                            float (&part)[NSLOT]) {
+  ngroup = 0;
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) {
+    kahan_add(sum[k], comp[k], part[k]);
+    part[k] = 0.0f;
+  }
+}
+
 // 3-node Gauss-Hermite (nodes 0, +-t, t^2 = 3/2, weights 4 w1, w1):
 //   (a w1/pi) [4/r2 + 2q/p],  q = r2 + t^2,  p = ((u-t)^2+a^2)((u+t)^2+a^2).
 // With u^2 = r2 - a^2 both factors are polynomials in r2 alone:
@@ -275,6 +287,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
 // relative error < 5e-7 over 100 <= r2 < 1e6.
 struct Gh3Line {
   float a2, C, c3, c45, c2;
+  Gh3Line() = default;
+  __device__ __forceinline__ Gh3Line(float a2_, float C_, float c3_, float c45_, float c2_)
+      : a2(a2_), C(C_), c3(c3_), c45(c45_), c2(c2_) {}
   __device__ __forceinline__ Gh3Line(float a2_, float P3) {
     const float P3h = 2.0f * P3;
     a2 = a2_;
@@ -302,7 +317,7 @@ struct Gh3Line {
 // first line, count); an item without lines gets one empty chunk so that its
 // tile is still written, and an exhausted item counter ends the stream with
 // an empty chunk of item -1.
-constexpr int F32_STAGES = 6;
+constexpr int F32_STAGES = 5;
 
 struct ChunkHdr {
   int item, l0, cnt, pad;
@@ -368,6 +383,19 @@ __device__ void f32_drain(F32Pipe &P, int *flags) {
   }
 }
 
+// What one warp needs of one line, prepared by one lane (lanes in parallel)
+// and read by the whole warp with three broadcast loads: the method class of
+// the (line, warp) pair, the covered points, the exact offset
+// d0 = wbase - c (the lane adds its own index), and the method's constants.
+struct __align__(16) WarpLine {
+  int code;          // 0: the line misses the warp; else class | full << 2
+  int lo, hi;        // covered points (grid indices)
+  float d0;          // (float)(wbase - c), exact
+  float beta, nphi, a2;
+  float q0, q1, q2, q3;  // GH1: P1; GH3: C, c3, c45, c2 (Gh3Line); mixed: P1
+  int j;             // the line's index in the chunk
+};
+
 // MINB resident CTAs per SM: 3 (<= 85 registers a thread) or 2.
 template <int BLOCK, int NSLOT, int LCH, bool COUNT, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB)
@@ -387,6 +415,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   static_assert(LCH % 32 == 0 && LPL * 3 <= 32, "3 class bits per line in one word");
   __shared__ __align__(128) LineRec32 sl[F32_STAGES][LCH];
   __shared__ __align__(8) F32Pipe P;
+  __shared__ WarpLine s_wl[NW][32];
   const int lane = threadIdx.x & 31;
   const int nitems = (int)(ntiles * n_cond);
   if (threadIdx.x == 0) {
@@ -407,19 +436,18 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 
   // cur: the item being accumulated; -2 before the first chunk (-1 marks the
   // end of the stream, so a CTA that gets no item at all still sees a change)
-  int cur = -2, cond = 0, wbase = 0;
+  int cur = -2, wbase = 0;
   // No stream is longer than every item's chunks plus the end markers: a
   // longer one means a logic error, reported instead of looping.
-  const unsigned long long max_seq =
-      (unsigned long long)nitems * (unsigned long long)(nlines / LCH + 2) + 2 * F32_STAGES;
-  double *kappa = nullptr;
+  const uint32_t max_seq = (uint32_t)min(
+      (unsigned long long)nitems * (unsigned long long)(nlines / LCH + 2) + 2 * F32_STAGES, 0x7FFFFFFFull);
   // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
   // into part[k] (relative error <= 7 u) and Kahan-adds the partial into
   // (sum, comp); total relative error < 6e-7.
   float sum[NSLOT], comp[NSLOT], part[NSLOT];
   int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  for (unsigned long long seq = 0;; ++seq) {
+  for (uint32_t seq = 0;; ++seq) {
     const int s = (int)(seq % F32_STAGES);
     if (seq > max_seq) {
       if (lane == 0) {
@@ -428,14 +456,15 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       }
       return;
     }
-    if (!mbar_wait_bounded(smem_addr(&P.full[s]), (uint32_t)((seq / F32_STAGES) & 1u), &st->err_flags,
-                           WAIT_LIMIT)) {
+    if (!mbar_wait_bounded(smem_addr(&P.full[s]), (seq / F32_STAGES) & 1u, &st->err_flags, WAIT_LIMIT)) {
       if (lane == 0) f32_drain(P, &st->err_flags);
       return;
     }
     const ChunkHdr h = P.hdr[s];
     if (h.item != cur) {
       if (cur >= 0) {  // the previous tile is complete: write it
+        const int cond = cond_order[cur / ntiles];
+        double *kappa = kappa_all + (int64_t)cond * ngrid;
         const double scale = ldexp(weight, cst[cond].scale_exp);
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
@@ -457,8 +486,6 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       }
       if (h.item < 0) return;  // end of the stream
       cur = h.item;
-      cond = cond_order[cur / ntiles];
-      kappa = kappa_all + (int64_t)cond * ngrid;
       wbase = (int)((cur % ntiles) * TILE) + (threadIdx.x >> 5) * WSPAN;
 #pragma unroll
       for (int k = 0; k < NSLOT; ++k) {
@@ -471,96 +498,129 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     if (lane == 0) P.pending[s] = 0;
     const LineRec32 *buf = sl[s];
     const int cnum = h.cnt;
-    // Method class of (line j, this warp) for the chunk's lines, lane l
-    // taking lines l, l + 32, ...: 3 bits (class, and whether the line covers
-    // the warp's whole span).  The extreme r^2 over the warp's covered points
-    // [lo, hi] decides it: r^2(d) is monotone on each side of the line centre
-    // in the FP32 arithmetic of the evaluation loops.
-    uint32_t mycls = 0;
-#pragma unroll
-    for (int m = 0; m < LPL; ++m) {
-      const int j = lane + 32 * m;
+    // The chunk in groups of 32 lines: lane l prepares line 32 m + l for this
+    // warp (method class: the extreme r^2 over the warp's covered points
+    // [lo, hi] decides it, r^2(d) being monotone on each side of the line
+    // centre in the FP32 arithmetic of the evaluation loops), then the warp
+    // runs through the group.
+    WarpLine *wl = s_wl[threadIdx.x >> 5];
+    const float lanef = (float)lane;
+    for (int m0 = 0; m0 < cnum; m0 += 32) {
+    int n1, n13, nall;
+    {
+      const int j = m0 + lane;
+      WarpLine r;
+      r.code = 0;
       if (j < cnum) {
-        const int c = buf[j].c;
-        const int lo = max(buf[j].ilo, wbase), hi = min(buf[j].ihi, wbase + WSPAN - 1);
+        const LineRec32 &L = buf[j];
+        const int c = L.c;
+        const int lo = max(L.ilo, wbase), hi = min(L.ihi, wbase + WSPAN - 1);
         if (lo <= hi) {
-          const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
+          const float beta = L.beta, nphi = -L.phi_k, a2 = L.a2;
           const int dlo = lo - c, dhi = hi - c;
           const int dnear = dlo >= 1 ? dlo : (dhi <= -1 ? dhi : 0);
           const float un = fmaf((float)dnear, beta, nphi);
           const float ul = fmaf((float)dlo, beta, nphi), uh = fmaf((float)dhi, beta, nphi);
           const float r2near = fmaf(un, un, a2);
           const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
-          const uint32_t cls = r2near >= 1.0e6f ? CLS_GH1
-                                                : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
-          const uint32_t full = (lo == wbase) && (hi == wbase + WSPAN - 1);
-          mycls |= (cls | (full << 2)) << (3 * m);
+          const int cls = r2near >= 1.0e6f ? CLS_GH1
+                                           : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
+          const int full = (lo == wbase) && (hi == wbase + WSPAN - 1);
+          r.code = cls | (full << 2);
+          r.lo = lo;
+          r.hi = hi;
+          r.d0 = (float)(wbase - c);
+          r.beta = beta;
+          r.nphi = nphi;
+          r.a2 = a2;
+          r.j = j;
+          if (cls == CLS_GH3) {
+            const Gh3Line g3(a2, L.P3);
+            r.q0 = g3.C;
+            r.q1 = g3.c3;
+            r.q2 = g3.c45;
+            r.q3 = g3.c2;
+          } else {
+            r.q0 = L.P1;
+          }
         }
       }
+      // records ordered by kind: whole-span GH1 lines, whole-span GH3
+      // lines, then the rest; lines that miss the warp are dropped
+      const bool g1 = r.code == (CLS_GH1 | 4), g3 = r.code == (CLS_GH3 | 4);
+      const bool ot = r.code != 0 && !g1 && !g3;
+      const unsigned b1 = __ballot_sync(0xffffffffu, g1), b3 = __ballot_sync(0xffffffffu, g3);
+      const unsigned bo = __ballot_sync(0xffffffffu, ot);
+      const unsigned lt = (1u << lane) - 1u;
+      n1 = __popc(b1);
+      n13 = n1 + __popc(b3);
+      nall = n13 + __popc(bo);
+      const int pos = g1 ? __popc(b1 & lt) : (g3 ? n1 + __popc(b3 & lt) : n13 + __popc(bo & lt));
+      if (r.code) wl[pos] = r;
     }
-    for (int j = 0; j < cnum; ++j) {
-      const uint32_t code = (__shfl_sync(0xffffffffu, mycls, j & 31) >> (3 * (j >> 5))) & 7u;
-      if (code == 0) continue;  // warp-uniform: the line misses this warp
-      if (++ngroup == KAHAN_GROUP) {
-        ngroup = 0;
+    __syncwarp();
+    // whole-span GH1 lines: 5 instructions an evaluation
+    for (int t = 0; t < n1; ++t) {
+      const WarpLine &W = wl[t];
+      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2, P1 = W.q0;
+#pragma unroll
+      for (int k = 0; k < NSLOT; ++k) {
+        const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+        part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
+      }
+      if (COUNT) cnt[2] += NSLOT;
+    }
+    // whole-span GH3 lines: 10 instructions an evaluation
+    for (int t = n1; t < n13; ++t) {
+      const WarpLine &W = wl[t];
+      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2;
+      const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
+#pragma unroll
+      for (int k = 0; k < NSLOT; ++k) {
+        const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+        part[k] = g3.add(part[k], fmaf(u, u, a2));
+      }
+      if (COUNT) cnt[1] += NSLOT;
+    }
+    // the rest: GH1 or GH3 lines covering part of the span, and lines with a
+    // method boundary or their core in the span
+    for (int jj = n13; jj < nall; ++jj) {
+      const WarpLine &W = wl[jj];
+      const int cls = W.code & 3;
+      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      const int lo = W.lo, hi = W.hi;
+      const float beta = W.beta, nphi = W.nphi, a2 = W.a2;
+      // (i - c) of this lane's first point, exact in FP32
+      const float d0 = W.d0 + lanef;
+      if (cls == CLS_GH1) {
+        const float P1 = W.q0;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
-          kahan_add(sum[k], comp[k], part[k]);
-          part[k] = 0.0f;
-        }
-      }
-      const int cls = (int)(code & 3u);
-      const bool full = (code & 4u) != 0;
-      const int ilo = buf[j].ilo, ihi = buf[j].ihi, c = buf[j].c;
-      const int lo = max(ilo, wbase), hi = min(ihi, wbase + WSPAN - 1);
-      const float beta = buf[j].beta, nphi = -buf[j].phi_k, a2 = buf[j].a2;
-      // (i - c) of this lane's first point, exact in FP32
-      const float d0 = (float)(wbase + lane - c);
-      if (cls == CLS_GH1) {
-        const float P1 = buf[j].P1;
-        if (full) {
-#pragma unroll
-          for (int k = 0; k < NSLOT; ++k) {
-            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-            const float r2 = fmaf(u, u, a2);
-            part[k] += P1 * fast_rcp(r2);
-          }
-          if (COUNT) cnt[2] += NSLOT;
-        } else {
-#pragma unroll
-          for (int k = 0; k < NSLOT; ++k) {
-            const int i = wbase + lane + 32 * k;
-            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-            const float r2 = fmaf(u, u, a2);
-            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
-            part[k] += in ? P1 * fast_rcp(r2) : 0.0f;
-            if (COUNT) cnt[2] += in;
-          }
+          const int i = wbase + lane + 32 * k;
+          const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+          const float r2 = fmaf(u, u, a2);
+          const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+          part[k] += in ? P1 * fast_rcp(r2) : 0.0f;
+          if (COUNT) cnt[2] += in;
         }
       } else if (cls == CLS_GH3) {
-        const Gh3Line g3(a2, buf[j].P3);
-        if (full) {
+        const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
 #pragma unroll
-          for (int k = 0; k < NSLOT; ++k) {
-            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-            part[k] = g3.add(part[k], fmaf(u, u, a2));
-          }
-          if (COUNT) cnt[1] += NSLOT;
-        } else {
-#pragma unroll
-          for (int k = 0; k < NSLOT; ++k) {
-            const int i = wbase + lane + 32 * k;
-            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-            const float r2 = fmaf(u, u, a2);
-            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
-            part[k] = in ? g3.add(part[k], r2) : part[k];
-            if (COUNT) cnt[1] += in;
-          }
+        for (int k = 0; k < NSLOT; ++k) {
+          const int i = wbase + lane + 32 * k;
+          const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+          const float r2 = fmaf(u, u, a2);
+          const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+          part[k] = in ? g3.add(part[k], r2) : part[k];
+          if (COUNT) cnt[1] += in;
         }
       } else {
         // Per point: GH1, GH3 or, in the core, Algorithm 916 (or the
         // surrogate's queue when routed).
-        const float P1 = buf[j].P1;
+        const int j = W.j;
+        const float P1 = W.q0;
         const Gh3Line g3(a2, buf[j].P3);
         const int srow = surr_row(sq, buf[j].a);
 #pragma unroll
@@ -581,7 +641,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
                 const unsigned long long slot = surr_reserve(sq);
                 if (slot < sq->cap) {
                   sq->idx[slot] = i;
-                  sq->cond[slot] = cond;
+                  sq->cond[slot] = cond_order[cur / ntiles];
                   sq->w[slot] = buf[j].Sp;
                   sq->x[slot] = fabsf(u);
                   sq->y[slot] = buf[j].a;
@@ -599,6 +659,8 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           }
         }
       }
+    }
+    __syncwarp();  // the group's records are overwritten next
     }
     // release the stage; the last warp out refills it
     __syncwarp();
@@ -673,7 +735,7 @@ static int pick_nslot(int64_t n, int block, int ppt, int slots) {
 // that the number of tiles can be matched to whole waves of resident CTAs
 // (equal tiles finish together, so a partial last wave idles the rest of the
 // GPU).  X(NSLOT, resident CTAs per SM the kernel is compiled for).
-#define HELK_F32_NSLOTS(X) X(6, 3) X(7, 3) X(8, 3) X(9, 3) X(10, 3) X(11, 3) X(12, 3) X(13, 3) X(14, 3) X(16, 2)
+#define HELK_F32_NSLOTS(X) X(6, 3) X(7, 3) X(8, 3) X(9, 2) X(10, 2) X(11, 2) X(12, 2) X(13, 2) X(14, 2) X(16, 2)
 constexpr int F32_COUNT_NSLOT = 8;  // the counting variant (statistics) uses one tile shape
 
 template <int NS, int MB>
