@@ -249,6 +249,25 @@ __device__ __forceinline__ unsigned long long surr_reserve(SurrQueue *sq) {
   return g.shfl(base, 0) + g.thread_rank();
 }
 
+// One core evaluation (x^2 + y^2 < 100): S' K by Algorithm 916, or 0 after
+// appending the point to the surrogate's queue when its cell is validated
+// (the queue's kernel adds it later).
+__device__ __forceinline__ float core_point(const LineRec32 &L, float x, int i, int srow, SurrQueue *sq,
+                                         int cond) {
+  if (srow >= 0 && surr_route(sq, srow, x)) {
+    const unsigned long long slot = surr_reserve(sq);
+    if (slot < sq->cap) {
+      sq->idx[slot] = i;
+      sq->cond[slot] = cond;
+      sq->w[slot] = L.Sp;
+      sq->x[slot] = x;
+      sq->y[slot] = L.a;
+      return 0.0f;
+    }
+  }
+  return L.Sp * k916_f32(x, L.a, L.erfcx_a, L.sig1);
+}
+
 // Hardware reciprocal approximation (max relative error ~1 ulp); every
 // argument here is >= 100, far from the denormal range.
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -264,16 +283,21 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
-// Kahan-adds the group's partials into (sum, comp) and restarts the group.
+// Makes room for n more lines in the plain partials: when the group would
+// exceed KAHAN_GROUP lines, Kahan-adds the partials into (sum, comp) and
+// starts a new group.
 template <int NSLOT>
-__device__ __forceinline__ void kahan_flush(int &ngroup, float (&sum)[NSLOT], float (&comp)[NSLOT],
-                                            float (&part)[NSLOT]) {
-  ngroup = 0;
+__device__ __forceinline__ void kahan_room(int &ngroup, int n, float (&sum)[NSLOT], float (&comp)[NSLOT],
+                                           float (&part)[NSLOT]) {
+  if (ngroup + n > KAHAN_GROUP) {
+    ngroup = 0;
 #pragma unroll
-  for (int k = 0; k < NSLOT; ++k) {
-    kahan_add(sum[k], comp[k], part[k]);
-    part[k] = 0.0f;
+    for (int k = 0; k < NSLOT; ++k) {
+      kahan_add(sum[k], comp[k], part[k]);
+      part[k] = 0.0f;
+    }
   }
+  ngroup += n;
 }
 
 // 3-node Gauss-Hermite (nodes 0, +-t, t^2 = 3/2, weights 4 w1, w1):
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     // whole-span GH1 lines: 5 instructions an evaluation
     for (int t = 0; t < n1; ++t) {
       const WarpLine &W = wl[t];
-      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
       const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2, P1 = W.q0;
 #pragma unroll
       for (int k = 0; k < NSLOT; ++k) {
@@ -574,7 +598,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     // whole-span GH3 lines: 10 instructions an evaluation
     for (int t = n1; t < n13; ++t) {
       const WarpLine &W = wl[t];
-      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
       const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2;
       const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
 #pragma unroll
@@ -589,7 +613,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     for (int jj = n13; jj < nall; ++jj) {
       const WarpLine &W = wl[jj];
       const int cls = W.code & 3;
-      if (++ngroup == KAHAN_GROUP) kahan_flush<NSLOT>(ngroup, sum, comp, part);
+      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
       const int lo = W.lo, hi = W.hi;
       const float beta = W.beta, nphi = W.nphi, a2 = W.a2;
       // (i - c) of this lane's first point, exact in FP32
@@ -636,22 +660,10 @@ __global__ void __launch_bounds__(BLOCK, MINB)
               part[k] = g3.add(part[k], r2);
               if (COUNT) cnt[1]++;
             } else {
-              bool routed = false;
-              if (srow >= 0 && surr_route(sq, srow, fabsf(u))) {
-                const unsigned long long slot = surr_reserve(sq);
-                if (slot < sq->cap) {
-                  sq->idx[slot] = i;
-                  sq->cond[slot] = cond_order[cur / ntiles];
-                  sq->w[slot] = buf[j].Sp;
-                  sq->x[slot] = fabsf(u);
-                  sq->y[slot] = buf[j].a;
-                  routed = true;
-                }
-              }
-              if (!routed) part[k] += buf[j].Sp * k916_f32(fabsf(u), buf[j].a, buf[j].erfcx_a, buf[j].sig1);
+              part[k] += core_point(buf[j], fabsf(u), i, srow, sq, cond_order[cur / ntiles]);
               if (COUNT) {
                 int n0, n1;
-                a916_range(fabs((double)u), n0, n1);
+                a916_range_f32(fabsf(u), n0, n1);
                 cnt[0]++;
                 cnt[3] += (unsigned long long)(n1 - n0 + 1);
               }

@@ -57,9 +57,20 @@ static __device__ __noinline__ double k916_f64(double x, double y, double erfcx_
   return K;
 }
 
-// The same series in FP32 (accurate expf/sincosf; recurrences start at the
-// low end of the summed range, where the terms are ~e^{-38}, so nothing
-// overflows or underflows in FP32).
+// The same series in FP32 (accurate expf/sincosf).  Only the terms within
+// A916_TAIL_F32 = 4.3 of the Gaussian peaks are summed (each dropped term is
+// below e^{-18.49} = 9.3e-9 of its weight): the truncation is below 3e-9 of K
+// over x^2 + y^2 < 100, y >= 1e-8 (against the exact w(z), in FP64), under
+// FP32 resolution.  The recurrences start at the low end of the summed range
+// (terms ~e^{-18.5}), so nothing overflows or underflows.
+constexpr float A916_TAIL_F32 = 4.3f;
+
+static __device__ __forceinline__ void a916_range_f32(float x, int &n0, int &n1) {
+  n0 = (int)floorf((x - A916_TAIL_F32) * 2.0f);
+  if (n0 < 1) n0 = 1;
+  n1 = (int)ceilf((x + A916_TAIL_F32) * 2.0f);
+}
+
 static __device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
   const float h = 0.5f;
   const float ex2 = expf(-(x * x));
@@ -68,9 +79,8 @@ static __device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, f
   sincosf(xy, &s, &c);
   const float sinc = (xy == 0.0f) ? 1.0f : s / xy;
   const float c2xy = c * c - s * s;
-  int n0 = (int)floorf((x - 6.2f) * 2.0f);
-  if (n0 < 1) n0 = 1;
-  const int n1 = (int)ceilf((x + 6.2f) * 2.0f);
+  int n0, n1;
+  a916_range_f32(x, n0, n1);
   const float q = 0.60653065971f;  // e^{-2h^2}
   const float nh = n0 * h;
   const float dm = nh - x, dp = nh + x;
