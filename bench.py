@@ -295,7 +295,8 @@ def run_ours(args):
         voigt_s = voigt_ms / max(1, voigt_n) * 1e-3
         peak = FMA_PER_CLK_SM[form] * 2 * nsm * max_mhz * 1e6 / 1e12
         achieved = flops / voigt_s / 1e12
-        src = os.path.join(ROOT, "paper_1503_03806_gb300", "csrc", "k_voigt.cu")
+        src = os.path.join(ROOT, "paper_1503_03806_gb300", "csrc",
+                           "k_voigt.cu" if form == "f32" else "k_voigt64.cu")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic_from_profile(src, os.path.join(ROOT, "profiles",

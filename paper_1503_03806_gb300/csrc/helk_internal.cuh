@@ -269,6 +269,12 @@ int voigt_tile_candidates(int precision, int *out, int max);
 // condition k at kappa + k * g.n.
 cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
                          double *kappa, int tile_len, int64_t ntiles);
+// k_voigt64.cu: the FP64 form (called by the dispatch above) and the
+// bounded-wait self-test
+int f64_tile_candidates(int *out, int max);
+int f64_tile_len(helk_ctx *c, int count, int64_t n);
+cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa,
+                             int tile_len, int64_t ntiles);
 cudaError_t launch_selftest_timeout(helk_ctx *c, int polls);
 // k_kdist.cu
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
