@@ -41,32 +41,73 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------- logarithm --
-// ln x for a positive normal double by the table-driven method of Tang
-// (ACM TOMS 16(4), 1990): x = 2^e m with m in [1, 2), c_j = 1 + j/128 where j
-// is the top 7 fraction bits of m, so f = m - c_j is exact and
-// r = f / c_j lies in [0, 1/128); then ln x = e ln2 + ln c_j + log1p(r) with
-// log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6 + r^4/7) (truncation
-// < 2^-59 relative to r).  r and r^2/2 are FP64; the cubic remainder
-// (< 2^-21) is FP32, absolute error < 2^-44.  The 128 entries ln c_j, 1/c_j
-// live in shared memory.  Subnormal arguments take the library log.
-constexpr double LOG_LN2 = 0.69314718055994530941723;
+// ln x for a positive double by the table-driven method of Tang (ACM TOMS
+// 16(4), 1990): x = 2^e m with m in [1, 2), c_j = 1 + j/128 where j is the
+// top 7 fraction bits of m, so f = m - c_j is exact and r = f / c_j lies in
+// [0, 1/128); then ln x = e ln2 + ln c_j + log1p(r), with log1p(r) to r^7
+// (truncation < 2^-59).  The 128 entries ln c_j, 1/c_j live in shared memory.
+// It is computed as an FP32 (high, low) pair with integer and FP32
+// operations only (FP64 runs at 1/64 of the FP32 rate here).  From the
+// key bits: e, j and f = F 2^-52 with F the 45 fraction bits below j, split
+// exactly into two floats; r = f (1/c_j) in float-float (1/c_j as a pair);
+// ln x = e ln2 + ln c_j + r - r^2/2 + r^3 q(r), the large terms added by
+// two-sum, ln2 in three parts (the first with 12 bits, so e * ln2_hi is
+// exact), the cubic remainder (< 2^-21) in plain FP32.  Absolute error
+// < 2e-12 for |ln x| < 70, < 2e-11 over the normal range (float-float
+// resolution of |ln x|).
+constexpr float LN2_HI_F = 0x1.62ep-1f;      // 2839/4096
+constexpr float LN2_MID_F = 0x1.0bfbe8p-15f;
+constexpr float LN2_LO_F = 0x1.cf78p-40f;
 
-__device__ __forceinline__ double log_table(double x, const double *lnc, const double *invc) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return log(x);
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float2 log_ff(unsigned long long b, const float2 *lnc, const float2 *invc) {
+  const int ex = (int)(b >> 52);
+  if (ex == 0) {  // subnormal: the library log, then split
+    const double L = log(__longlong_as_double((long long)b));
+    const float hi = (float)L;
+    return make_float2(hi, (float)(L - (double)hi));
+  }
   const int j = (int)((b >> 45) & 0x7F);
-  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
-  const double cj = __longlong_as_double(0x3FF0000000000000LL | ((long long)j << 45));
-  const double r = (m - cj) * invc[j];
-  const float rf = (float)r;
-  float q = fmaf(rf, 1.0f / 7.0f, -1.0f / 6.0f);
-  q = fmaf(q, rf, 1.0f / 5.0f);
-  q = fmaf(q, rf, -1.0f / 4.0f);
-  q = fmaf(q, rf, 1.0f / 3.0f);
-  const float cub = (rf * rf) * (rf * q);
-  const double p = fma(-0.5 * r, r, (double)cub) + r;
-  return fma((double)(ex - 1023), LOG_LN2, lnc[j] + p);
+  const unsigned long long F = b & 0x1FFFFFFFFFFFull;
+  const float fh = (float)(unsigned)(F >> 21) * 0x1p-31f;        // top 24 bits, exact
+  const float fl = (float)(unsigned)(F & 0x1FFFFFu) * 0x1p-52f;  // low 21 bits, exact
+  const float2 ic = invc[j];
+  float rh = fh * ic.x;
+  float rl = fmaf(fh, ic.x, -rh);
+  rl = fmaf(fh, ic.y, rl);
+  rl = fmaf(fl, ic.x, rl);
+  {
+    const float t = rh + rl;  // |rh| >= |rl|
+    rl = rl - (t - rh);
+    rh = t;
+  }
+  const float p = rh * rh;
+  float pe = fmaf(rh, rh, -p);
+  pe = fmaf(2.0f * rh, rl, pe);
+  float q = fmaf(rh, 1.0f / 7.0f, -1.0f / 6.0f);
+  q = fmaf(q, rh, 1.0f / 5.0f);
+  q = fmaf(q, rh, -1.0f / 4.0f);
+  q = fmaf(q, rh, 1.0f / 3.0f);
+  const float cub = (rh * rh) * (rh * q);
+  const float2 lc = lnc[j];
+  const float ef = (float)(ex - 1023);
+  const float mh = ef * LN2_MID_F;
+  const float ml = fmaf(ef, LN2_MID_F, -mh);
+  float s, e1, e2, e3, e4;
+  two_sum_f(ef * LN2_HI_F, lc.x, s, e1);
+  two_sum_f(s, mh, s, e2);
+  two_sum_f(s, rh, s, e3);
+  two_sum_f(s, -0.5f * p, s, e4);
+  float lo = ((e1 + e2) + (e3 + e4)) + (lc.y + ml);
+  lo = fmaf(ef, LN2_LO_F, lo);
+  lo = fmaf(-0.5f, pe, lo + rl) + cub;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
 }
 
 // ------------------------------------------------------ pseudo-inverse --
@@ -386,7 +427,7 @@ __global__ void __launch_bounds__(KD_THREADS)
   __shared__ uint32_t wtot[32];
   __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
   __shared__ double red[KD_WARPS][NCHEB_MAX + 1];
-  __shared__ double s_lnc[128], s_invc[128];
+  __shared__ float2 s_lnc[128], s_invc[128];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t off = (int64_t)blockIdx.x * nb;
   unsigned long long *A = MODE == 0 ? (unsigned long long *)dsm : gA + off;
@@ -397,10 +438,11 @@ __global__ void __launch_bounds__(KD_THREADS)
     vand &= k;
     vor |= k;
   }
-  if (tid < 128) {
-    const double cj = 1.0 + tid / 128.0;
-    s_lnc[tid] = log(cj);
-    s_invc[tid] = 1.0 / cj;
+  if (tid < 128) {  // ln c_j and 1/c_j as FP32 (high, low) pairs
+    const double cj = 1.0 + tid / 128.0, l = log(cj), ic = 1.0 / cj;
+    const float lh = (float)l, ih = (float)ic;
+    s_lnc[tid] = make_float2(lh, (float)(l - (double)lh));
+    s_invc[tid] = make_float2(ih, (float)(ic - (double)ih));
   }
   for (int o = 16; o > 0; o >>= 1) {
     vand &= __shfl_down_sync(0xffffffffu, vand, o);
@@ -427,13 +469,14 @@ __global__ void __launch_bounds__(KD_THREADS)
   // sorted values out, the bin sum, and L_j in place as a split pair
   double ksum = 0.0;
   float2 *Ls = reinterpret_cast<float2 *>(S);
+  const unsigned long long floor_bits = (unsigned long long)__double_as_longlong(kappa_floor);
   for (int j = tid; j < nb; j += KD_THREADS) {
-    const double kv = __longlong_as_double((long long)S[j]);
+    const unsigned long long kb = S[j];
+    const double kv = __longlong_as_double((long long)kb);
     if (kg_out) kg_out[off + j] = kv;
     ksum += kv;
-    const double L = log_table(kv > kappa_floor ? kv : kappa_floor, s_lnc, s_invc);
-    const float hi = (float)L;
-    Ls[j] = make_float2(hi, (float)(L - (double)hi));
+    // non-negative doubles order as their bit patterns: max(k, floor) on the bits
+    Ls[j] = log_ff(kb > floor_bits ? kb : floor_bits, s_lnc, s_invc);
   }
   {
     const double v = warp_sum(ksum);
