@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
       __syncthreads();
     }
   }
-  // P[:, j] = R^{-1} Q_1[j, :]^T, stored k-major (P[k*nb + j]) as split pairs
+  // P[:, j] = R^{-1} Q_1[j, :]^T, k-major (P[k*nb + j])
   for (int64_t j = tid; j < nb; j += PI_THREADS) {
     double p[NCHEB_MAX];
     for (int k = ncheb - 1; k >= 0; --k) {
@@ -201,13 +201,26 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
       for (int m = k + 1; m < ncheb; ++m) v -= R[k * NCHEB_MAX + m] * p[m];
       p[k] = v / R[k * NCHEB_MAX + k];
     }
-    // stored as FP32 (high, low) pairs, high = fl32(P), low = fl32(P - high)
-    float2 *Ps = reinterpret_cast<float2 *>(P);
-    for (int k = 0; k < ncheb; ++k) {
-      const float hi = (float)p[k];
-      Ps[(int64_t)k * nb + j] = make_float2(hi, (float)(p[k] - (double)hi));
-    }
+    for (int k = 0; k < ncheb; ++k) P[(int64_t)k * nb + j] = p[k];
   }
+  __syncthreads();
+  // The abscissae are symmetric, t_{nb-1-j} = -t_j, and T_k(-t) = (-1)^k T_k(t),
+  // so P[k][nb-1-j] = (-1)^k P[k][j]: only the symmetrized first half,
+  // j < nh = ceil(nb/2), is kept, as FP32 (high, low) pairs [k][nh], built in
+  // `work` and then moved to the front of P.
+  const int64_t nh = (nb + 1) / 2;
+  float2 *W = reinterpret_cast<float2 *>(work);
+  for (int64_t e = tid; e < (int64_t)ncheb * nh; e += PI_THREADS) {
+    const int k = (int)(e / nh);
+    const int64_t j = e % nh;
+    const double v =
+        0.5 * (P[(int64_t)k * nb + j] + ((k & 1) ? -1.0 : 1.0) * P[(int64_t)k * nb + (nb - 1 - j)]);
+    const float hi = (float)v;
+    W[e] = make_float2(hi, (float)(v - (double)hi));
+  }
+  __syncthreads();
+  float2 *Ps = reinterpret_cast<float2 *>(P);
+  for (int64_t e = tid; e < (int64_t)ncheb * nh; e += PI_THREADS) Ps[e] = W[e];
   if (tid == 0 && vtv_out) vtv_out[0] = vtv[0];
 }
 
@@ -401,6 +414,16 @@ __device__ void cta_sort_bin(unsigned long long *A, const double *__restrict__ s
   cta_radix_sort_reg(A, nb, hist, wtot, diff, 0);
 }
 
+// a + b for float-float pairs (two-sum of the high parts, low parts added)
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  float e = (a.x - (s - bb)) + (b.x - bb);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
 // c_k += P_kj L_j in double-float: (sh, sl) holds the running sum; the
 // product of the high parts is exact as p + e (two-product), p joins sh by
 // two-sum, and e, the two-sum error and the cross terms go to sl.
@@ -483,16 +506,26 @@ __global__ void __launch_bounds__(KD_THREADS)
     if (lane == 0) red[w][NCHEB_MAX] = v;
   }
   __syncthreads();
-  // c = P L, eight coefficients per sweep over the points
+  // c = P L, eight coefficients per sweep over the first half of the points:
+  // c_k = sum_{j < nh} P[k][j] (L_j + (-1)^k L_{nb-1-j}) (the middle point of
+  // an odd bin once), P holding the symmetrized half [k][nh]
+  const int nh = (nb + 1) >> 1;
   for (int k0 = 0; k0 < ncheb; k0 += 8) {
     float sh[8], sl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
-    for (int j = tid; j < nb; j += KD_THREADS) {
-      const float2 L = Ls[j];
+    for (int j = tid; j < nh; j += KD_THREADS) {
+      const float2 La = Ls[j];
+      const int jm = nb - 1 - j;
+      float2 Lp = La, Lm = La;
+      if (jm != j) {
+        const float2 Lb = Ls[jm];
+        Lp = ff_add(La, Lb);
+        Lm = ff_add(La, make_float2(-Lb.x, -Lb.y));
+      }
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], P[(int64_t)(k0 + q) * nb + j], L);
+        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], P[(int64_t)(k0 + q) * nh + j], (q & 1) ? Lm : Lp);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
