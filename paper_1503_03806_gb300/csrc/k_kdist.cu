@@ -424,6 +424,20 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
   return make_float2(hi, e - (hi - s));
 }
 
+// L_j + L_{nb-1-j} and L_j - L_{nb-1-j} (the middle point of an odd bin:
+// L_j alone) as float-float pairs
+__device__ __forceinline__ void fold_pair(const float2 *Ls, int nb, int j, float2 &Lp, float2 &Lm) {
+  const float2 La = Ls[j];
+  const int jm = nb - 1 - j;
+  Lp = La;
+  Lm = La;
+  if (jm != j) {
+    const float2 Lb = Ls[jm];
+    Lp = ff_add(La, Lb);
+    Lm = ff_add(La, make_float2(-Lb.x, -Lb.y));
+  }
+}
+
 // c_k += P_kj L_j in double-float: (sh, sl) holds the running sum; the
 // product of the high parts is exact as p + e (two-product), p joins sh by
 // two-sum, and e, the two-sum error and the cross terms go to sl.
@@ -514,18 +528,26 @@ __global__ void __launch_bounds__(KD_THREADS)
     float sh[8], sl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
-    for (int j = tid; j < nh; j += KD_THREADS) {
-      const float2 La = Ls[j];
-      const int jm = nb - 1 - j;
-      float2 Lp = La, Lm = La;
-      if (jm != j) {
-        const float2 Lb = Ls[jm];
-        Lp = ff_add(La, Lb);
-        Lm = ff_add(La, make_float2(-Lb.x, -Lb.y));
+    // two points a step, so that 16 loads of P are in flight per thread
+    for (int j = tid; j < nh; j += 2 * KD_THREADS) {
+      const int j2 = j + KD_THREADS;
+      float2 Pa[8], Pb[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        Pa[q] = k0 + q < ncheb ? P[(int64_t)(k0 + q) * nh + j] : make_float2(0.0f, 0.0f);
+        Pb[q] = (k0 + q < ncheb && j2 < nh) ? P[(int64_t)(k0 + q) * nh + j2] : make_float2(0.0f, 0.0f);
       }
+      float2 Lp, Lm;
+      fold_pair(Ls, nb, j, Lp, Lm);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], P[(int64_t)(k0 + q) * nh + j], (q & 1) ? Lm : Lp);
+        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pa[q], (q & 1) ? Lm : Lp);
+      if (j2 < nh) {
+        fold_pair(Ls, nb, j2, Lp, Lm);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pb[q], (q & 1) ? Lm : Lp);
+      }
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
