@@ -301,7 +301,7 @@ def run_ours(args):
                 "frac": achieved / peak,
                 "traffic": traffic_from_profile(src, os.path.join(ROOT, "profiles",
                                                                   "voigt_%s_medium.txt" % form)),
-                "kernel": "k_voigt_" + form,
+                "kernel": "k_voigt_f32 + k_core_f32 (the Voigt stage)" if form == "f32" else "k_voigt_f64",
                 "peak_basis": "%s pipe: %d FMA/clk/SM x %d SMs x %.0f MHz max clock (derived)"
                               % (form.upper(), FMA_PER_CLK_SM[form], nsm, max_mhz),
                 "flops_per_launch": flops, "voigt_ms_per_launch": voigt_s * 1e3,

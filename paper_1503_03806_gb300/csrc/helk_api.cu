@@ -145,7 +145,7 @@ void helk_destroy(helk_ctx *c) {
                   (void *)c->squeue, c->squeue_buf})
     if (p) cudaFree(p);
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
-                  c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->ckey,   c->tile_lo, c->tile_hi,
+                  c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
                   c->mean_dev, c->tmp};
   for (void *p : bufs)
@@ -325,9 +325,11 @@ static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts 
   HELK_TRY(ensure_conds(c, n_cond));
   HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
   HELK_TRY(ensure_buf(c, (void **)&c->ckey, &c->ckey_cap, std::max<int64_t>(c->nlines, 1) * 8, "line keys"));
-  if (o.precision == HELK_PREC_F32_KAHAN)
+  if (o.precision == HELK_PREC_F32_KAHAN) {
     HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
                         "FP32 line records"));
+    HELK_TRY(ensure_buf(c, (void **)&c->core_rng, &c->core_cap, nl * (int64_t)sizeof(int2), "line cores"));
+  }
   HELK_TRY(ensure_tiles(c, ntiles * n_cond));
   if (o.surrogate && !c->squeue) {
     // routed-evaluation queue: 2^24 entries (entries beyond it fall back to
@@ -362,7 +364,8 @@ static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single
   for (int k = 0; k < n_cond; ++k)
     HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->cstats[k].wmax, 0xFF, sizeof(long long), c->stream), "stats"));
   if (c->nlines > 0) {
-    HELK_TRY(cuda_check(c, launch_lineprep(c, n_cond, single, mass, *cut, *g), "lineprep"));
+    HELK_TRY(cuda_check(c, launch_lineprep(c, n_cond, single, mass, *cut, *g, o.precision != HELK_PREC_F32_KAHAN),
+                        "lineprep"));
     if (o.precision == HELK_PREC_F32_KAHAN) HELK_TRY(cuda_check(c, launch_pack32(c, n_cond, *g), "pack32"));
   }
   return HELK_OK;
@@ -378,6 +381,7 @@ static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const 
   if (o.surrogate)
     HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->squeue->count, 0, sizeof(unsigned long long), c->stream), "voigt"));
   HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+  HELK_TRY(cuda_check(c, launch_voigt_core(c, n_cond, *g, o, kappa), "voigt cores"));
   if (o.surrogate) HELK_TRY(cuda_check(c, launch_mlp_queue(c, n_cond, g->n, o.weight, kappa), "surrogate"));
   return HELK_OK;
 }

@@ -103,7 +103,8 @@ struct CondStats {
   long long wmax;                   // max half-width of a window in points (-1: none)
   unsigned long long spmax_bits;    // max S' (non-negative double bits)
   int scale_exp;                    // FP32 form: strengths scaled by 2^-scale_exp
-  int pad;
+  int core_w1;                      // FP32 form: 1 + max distance (points) from a line's
+                                    // reference index to a point of its core, 0: no core
 };
 enum { ERRF_TIMEOUT = 1 };
 
@@ -127,6 +128,8 @@ struct helk_ctx {
   // per-call scratch
   helk::LineRec64 *rec64 = nullptr;
   helk::LineRec32 *rec32 = nullptr;
+  int2 *core_rng = nullptr;  // FP32 form: each line's core points [x, y] (x > y: none)
+  int64_t core_cap = 0;
   double *ckey = nullptr;
   int64_t ckey_cap = 0;
   int64_t rec_cap = 0, rec32_cap = 0;
@@ -251,8 +254,10 @@ cudaError_t launch_sort_lines(helk_ctx *c, int64_t n);  // orders SoA by nu0
 // n_cond conditions: from c->cond_dev, or (n_cond == 1 and single != NULL)
 // the one condition passed by value.  Records of condition k start at
 // k * nlines; tile maps at k * ntiles.
+// a916_f64: also the FP64 Algorithm 916 per-line factors (erfcx(a), S1(a)),
+// which only the FP64 form reads.
 cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, double mass,
-                            const helk_cutoff &cut, const helk_grid &g);
+                            const helk_cutoff &cut, const helk_grid &g, bool a916_f64);
 cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g);
 cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile, int64_t ntiles);
 // Conditions ordered by decreasing evaluation count (largest work first).
@@ -269,6 +274,9 @@ int voigt_tile_candidates(int precision, int *out, int max);
 // condition k at kappa + k * g.n.
 cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
                          double *kappa, int tile_len, int64_t ntiles);
+// FP32 form: the Algorithm 916 cores that k_voigt_f32 leaves out, added into
+// kappa (launched after launch_voigt; no-op for the FP64 form).
+cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa);
 // k_voigt64.cu: the FP64 form (called by the dispatch above) and the
 // bounded-wait self-test
 int f64_tile_candidates(int *out, int max);

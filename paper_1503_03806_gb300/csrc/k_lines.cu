@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "helk_internal.cuh"
+#include "voigt_common.cuh"
 
 namespace helk {
 
@@ -254,7 +255,7 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
                            const double *__restrict__ lweight, PrepArgs A,
                            const CondArgs *__restrict__ conds, CondArgs single,
                            LineRec64 *__restrict__ rec_all, double *__restrict__ ckey,
-                           CondStats *cst_all) {
+                           CondStats *cst_all, int a916_f64) {
   const int cond = blockIdx.y;
   const CondArgs C = conds ? conds[cond] : single;
   LineRec64 *rec = rec_all + (int64_t)cond * n;
@@ -310,8 +311,9 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
     r.Sp = Sp;
     r.ilo = (int32_t)lo;
     r.ihi = (int32_t)hi;
-    // Algorithm 916 per-line factors (only reachable when a < 10)
-    if (a < 10.0) {
+    // Algorithm 916 per-line factors (only reachable when a < 10); the FP32
+    // form takes them in FP32 when packing its records
+    if (a916_f64 && a < 10.0) {
       r.erfcx_a = erfcx(a);
       double s1 = 0.0;
       for (int k = 0; k < A916_S1_TERMS; ++k) {
@@ -362,7 +364,7 @@ static int line_blocks(helk_ctx *c, int64_t n, int n_cond) {
 }
 
 cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, double mass,
-                            const helk_cutoff &cut, const helk_grid &g) {
+                            const helk_cutoff &cut, const helk_grid &g, bool a916_f64) {
   const int64_t n = c->nlines;
   if (n <= 0) return cudaSuccess;
   PrepArgs A{mass, cut.kind, cut.value, cut.cap, g.nu_min, g.dnu, g.n};
@@ -372,7 +374,7 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
       n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair, c->has_gself ? c->gself : nullptr,
       c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr,
       c->has_mass ? c->lmass : nullptr, c->has_weight ? c->lweight : nullptr, A,
-      single ? nullptr : c->cond_dev, one, c->rec64, c->ckey, c->cstats);
+      single ? nullptr : c->cond_dev, one, c->rec64, c->ckey, c->cstats, a916_f64 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -383,7 +385,8 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // offset phi = (nu0' - nu_c) ku, so that u_i = (i - c) beta - phi keeps full
 // relative precision near the line centre.
 __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu,
-                         CondStats *cst_all, LineRec32 *__restrict__ r32_all) {
+                         const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
+                         int2 *__restrict__ core_all) {
   const int cond = blockIdx.y;
   const LineRec64 *r64 = r64_all + (int64_t)cond * n;
   LineRec32 *r32 = r32_all + (int64_t)cond * n;
@@ -391,6 +394,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
   const double spmax = __longlong_as_double((long long)cst->spmax_bits);
   const int E = spmax > 0.0 ? ilogb(spmax) + 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) cst->scale_exp = E;
+  int cw1 = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const LineRec64 r = r64[l];
@@ -409,58 +413,84 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     q.P1 = (float)(sp * r.a * INV_SQRTPI);
     q.P3 = (float)(sp * r.a * (SQRTPI / 6.0) / PI);
     q.Sp = (float)sp;
-    q.erfcx_a = (float)r.erfcx_a;
-    q.sig1 = (float)r.sig1;
+    if (q.a < 10.0f) {  // Algorithm 916 per-line factors, in FP32
+      q.erfcx_a = erfcxf(q.a);
+      float s1 = 0.0f;
+      for (int k = 0; k < A916_S1_TERMS; ++k) {
+        const float nh = (float)(k + 1) * (float)A916_H;
+        s1 += (float)c_exp_nh2[k] / (nh * nh + q.a2);
+      }
+      q.sig1 = s1;
+    } else {
+      q.erfcx_a = 0.0f;
+      q.sig1 = 0.0f;
+    }
     r32[l] = q;
+    // The line's core in the FP32 arithmetic of the Voigt kernels: points with
+    // fma(u, u, a^2) < 100, u = fma(i - c, beta, -phi), so |u| < 10 and
+    // |i - c| <= (10 + |phi|)/beta; the farthest such point from the
+    // reference index bounds the core kernel's candidate search.
+    int2 core = make_int2(1, 0);
+    if (q.a2 < 100.0f && q.ihi >= q.ilo && q.beta > 0.0f) {
+      const double dmax = ceil((10.001 + fabs((double)q.phi_k)) / (double)q.beta) + 1.0;
+      const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
+      if (clo <= chi) {
+        const double k = ckey[l];
+        const double w = fmax(k - clo, chi - k);
+        cw1 = max(cw1, (int)fmin(w + 1.0, 2.0e9));
+        core = make_int2((int)clo, (int)chi);
+      }
+    }
+    core_all[(int64_t)cond * n + l] = core;
   }
+  for (int o = 16; o > 0; o >>= 1) cw1 = max(cw1, __shfl_down_sync(0xffffffffu, cw1, o));
+  if ((threadIdx.x & 31) == 0 && cw1 > 0) atomicMax(&cst->core_w1, cw1);
 }
 
 cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   const int64_t n = c->nlines;
   if (n <= 0) return cudaSuccess;
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
-  k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->cstats, c->rec32);
+  k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->ckey, c->cstats, c->rec32,
+                                        c->core_rng);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- tile map --
 // Lines overlapping grid tile [A, B) have their reference index in
 // [A - W, B - 1 + W], W = max half-width of any window of the condition: a
-// contiguous range of the nu0-ordered list, found by two binary searches.
+// contiguous range of the nu0-ordered list, found by two searches.  One warp
+// per tile searches 32-ary: each step the lanes probe 32 evenly spaced keys
+// and a ballot narrows the range 32-fold (5 dependent loads for 1e6 lines
+// instead of 20 for a binary search).
+
 __global__ void k_tilemap(int64_t nlines, const double *__restrict__ ckey, int64_t ngrid, int tile,
                           int64_t ntiles, const CondStats *__restrict__ cst, int32_t *tlo,
                           int32_t *thi) {
   const int cond = blockIdx.y;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
+  const int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  if (t >= ntiles) return;  // warp-uniform
   const int64_t o = (int64_t)cond * ntiles + t;
-  long long W = cst[cond].wmax;
+  const long long W = cst[cond].wmax;
+  const int lane = threadIdx.x & 31;
   if (W < 0) {  // no line has a non-empty window
-    tlo[o] = 0;
-    thi[o] = 0;
+    if (lane == 0) tlo[o] = thi[o] = 0;
     return;
   }
-  double A = (double)(t * tile);
-  double B = (double)((t + 1) * tile < ngrid ? (t + 1) * tile : ngrid);
-  double klo = A - (double)W, khi = B - 1.0 + (double)W;
-  int64_t lo = 0, hi = nlines;  // first index with ckey >= klo
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (ckey[mid] < klo) lo = mid + 1; else hi = mid;
+  const double A = (double)(t * tile);
+  const double B = (double)((t + 1) * tile < ngrid ? (t + 1) * tile : ngrid);
+  const double klo = A - (double)W, khi = B - 1.0 + (double)W;
+  const int64_t first = warp_search(ckey, 0, nlines, klo, false);  // first key >= klo
+  const int64_t last = warp_search(ckey, first, nlines, khi, true); // first key > khi
+  if (lane == 0) {
+    tlo[o] = (int32_t)first;
+    thi[o] = (int32_t)last;
   }
-  int64_t first = lo;
-  lo = first; hi = nlines;      // first index with ckey > khi
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (ckey[mid] <= khi) lo = mid + 1; else hi = mid;
-  }
-  tlo[o] = (int32_t)first;
-  thi[o] = (int32_t)lo;
 }
 
 cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile, int64_t ntiles) {
-  dim3 grid((unsigned)((ntiles + 127) / 128), n_cond);
-  k_tilemap<<<grid, 128, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->cstats,
+  dim3 grid((unsigned)((ntiles + 7) / 8), n_cond);  // 8 warps, one tile each
+  k_tilemap<<<grid, 256, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->cstats,
                                          c->tile_lo, c->tile_hi);
   return cudaGetLastError();
 }

@@ -452,12 +452,11 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           if (COUNT) cnt[1] += in;
         }
       } else {
-        // Per point: GH1, GH3 or, in the core, Algorithm 916 (or the
-        // surrogate's queue when routed).
+        // Per point: GH1 or GH3; core points (r^2 < 100) are left to the
+        // core kernel, which evaluates them after this one.
         const int j = W.j;
         const float P1 = W.q0;
         const Gh3Line g3(a2, buf[j].P3);
-        const int srow = surr_row(sq, buf[j].a);
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
           const int i = wbase + lane + 32 * k;
@@ -470,14 +469,6 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             } else if (r2 >= 100.0f) {
               part[k] = g3.add(part[k], r2);
               if (COUNT) cnt[1]++;
-            } else {
-              part[k] += core_point(buf[j], fabsf(u), i, srow, sq, cond_order[cur / ntiles]);
-              if (COUNT) {
-                int n0, n1;
-                a916_range_f32(fabsf(u), n0, n1);
-                cnt[0]++;
-                cnt[3] += (unsigned long long)(n1 - n0 + 1);
-              }
             }
           }
         }
@@ -497,6 +488,83 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       }
     }
   }
+}
+
+// ------------------------------------------------- Algorithm 916 cores --
+// The points of every line's core (fma(u, u, a^2) < 100 in the FP32
+// arithmetic of k_voigt_f32, which skips exactly these points), one thread
+// per grid point: the candidate lines of a warp's 32 points are those whose
+// reference index lies within the condition's core reach of them (found by
+// the warp's own search), screened by each line's core range from the pack;
+// each thread adds S' K(|u|, a) of the lines whose core holds its point, in
+// list order (deterministic), or appends the point to the surrogate's queue
+// when routed.  Runs after k_voigt_f32 and
+// adds its sums (rescaled like the main kernel's) into kappa.  Few lines'
+// cores overlap at a point (~4 at the medium workload), so the plain FP32
+// sum loses < 1e-7 relative.
+constexpr int CORE_BLOCK = 256;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(CORE_BLOCK)
+    k_core_f32(const LineRec32 *__restrict__ rec_all, const int2 *__restrict__ core_all, int64_t nlines,
+               const double *__restrict__ ckey, int ngrid, double weight, double *__restrict__ kappa_all,
+               CondStats *cst, SurrQueue *sq) {
+  const int cond = blockIdx.y;
+  const int cw1 = cst[cond].core_w1;
+  if (cw1 == 0) return;  // no line of the condition has a core
+  // each warp finds its own 32 points' candidate lines: no CTA barrier
+  const int64_t A = (int64_t)blockIdx.x * CORE_BLOCK + (threadIdx.x & ~31);
+  if (A >= ngrid) return;  // warp-uniform
+  const int64_t B = min(A + 32, (int64_t)ngrid);
+  const double W = (double)(cw1 - 1);
+  const int64_t first = warp_search(ckey, 0, nlines, (double)A - W, false);
+  const int64_t last = warp_search(ckey, first, nlines, (double)(B - 1) + W, true);
+  const LineRec32 *rec = rec_all + (int64_t)cond * nlines;
+  const int2 *core = core_all + (int64_t)cond * nlines;
+  const int i = (int)(A + (threadIdx.x & 31));
+  float v = 0.0f;
+  unsigned long long n916 = 0, nterm = 0;
+  if (i < ngrid) {
+    for (int64_t l = first; l < last; ++l) {
+      const int2 cr = core[l];  // the line's core points, a superset of r^2 < 100
+      if (i < cr.x || i > cr.y) continue;
+      const LineRec32 &L = rec[l];
+      const float u = fmaf((float)(i - L.c), L.beta, -L.phi_k);
+      if (fmaf(u, u, L.a2) >= 100.0f) continue;
+      v += core_point(L, fabsf(u), i, surr_row(sq, L.a), sq, cond);
+      if (COUNT) {
+        int n0, n1;
+        a916_range_f32(fabsf(u), n0, n1);
+        ++n916;
+        nterm += (unsigned long long)(n1 - n0 + 1);
+      }
+    }
+    if (v != 0.0f)
+      kappa_all[(int64_t)cond * ngrid + i] += ldexp(weight, cst[cond].scale_exp) * (double)v;
+  }
+  if (COUNT) {
+    for (int o = 16; o > 0; o >>= 1) {
+      n916 += __shfl_down_sync(0xffffffffu, n916, o);
+      nterm += __shfl_down_sync(0xffffffffu, nterm, o);
+    }
+    if ((threadIdx.x & 31) == 0 && n916) {
+      atomicAdd(&cst[cond].region[0], n916);
+      atomicAdd(&cst[cond].region[3], nterm);
+    }
+  }
+}
+
+cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa) {
+  if (o.precision != HELK_PREC_F32_KAHAN || c->nlines <= 0) return cudaSuccess;
+  SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
+  const dim3 grid((unsigned)((g.n + CORE_BLOCK - 1) / CORE_BLOCK), (unsigned)n_cond);
+  if (o.count_regions)
+    k_core_f32<true><<<grid, CORE_BLOCK, 0, c->stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey, (int)g.n,
+                                                          o.weight, kappa, c->cstats, sq);
+  else
+    k_core_f32<false><<<grid, CORE_BLOCK, 0, c->stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey, (int)g.n,
+                                                           o.weight, kappa, c->cstats, sq);
+  return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- launch --

@@ -1,6 +1,7 @@
-// voigt_common.cuh -- pieces shared by the two Voigt kernel files: the
-// bounded-wait limit of the bulk-copy barriers and the occupancy helpers of
-// the persistent launches.
+// voigt_common.cuh -- pieces shared by the Voigt kernel files and the tile
+// map: the bounded-wait limit of the bulk-copy barriers, the occupancy
+// helpers of the persistent launches, and a warp-cooperative search of the
+// lines' sorted reference indices.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,6 +28,26 @@ template <typename K>
 static unsigned persistent_grid(helk_ctx *c, K kern, int block, int64_t nitems) {
   const int64_t slots = resident_ctas(c, kern, block);
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(slots, nitems));
+}
+
+// First index in [lo, hi) whose key is not below x (strict: key > x when
+// `upper`), else hi.  All lanes take part and get the result.
+__device__ __forceinline__ int64_t warp_search(const double *__restrict__ key, int64_t lo, int64_t hi, double x, bool upper) {
+  const int lane = threadIdx.x & 31;
+  // invariant: the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t p = lo + (int64_t)lane * step;
+    const bool below = p < hi && (upper ? key[p] <= x : key[p] < x);
+    const int c = __popc(__ballot_sync(0xffffffffu, below));
+    const int64_t nlo = c > 0 ? lo + (int64_t)(c - 1) * step + 1 : lo;
+    const int64_t nhi = c > 0 ? min(hi, lo + (int64_t)c * step) : lo;
+    lo = nlo;
+    hi = nhi;
+  }
+  const int64_t p = lo + lane;
+  const bool below = p < hi && (upper ? key[p] <= x : key[p] < x);
+  return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 
 }  // namespace helk

@@ -64,6 +64,7 @@ static __device__ __noinline__ double k916_f64(double x, double y, double erfcx_
 // FP32 resolution.  The recurrences start at the low end of the summed range
 // (terms ~e^{-18.5}), so nothing overflows or underflows.
 constexpr float A916_TAIL_F32 = 4.3f;
+constexpr int A916_TERMS_F32 = 20;  // n1 - n0 + 1 <= 2 (2 * 4.3 + 1) + 1 = 20.2
 
 static __device__ __forceinline__ void a916_range_f32(float x, int &n0, int &n1) {
   n0 = (int)floorf((x - A916_TAIL_F32) * 2.0f);
@@ -71,32 +72,36 @@ static __device__ __forceinline__ void a916_range_f32(float x, int &n0, int &n1)
   n1 = (int)ceilf((x + A916_TAIL_F32) * 2.0f);
 }
 
-static __device__ __noinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
+static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
   const float h = 0.5f;
   const float ex2 = expf(-(x * x));
   const float xy = x * y;
   float s, c;
   sincosf(xy, &s, &c);
-  const float sinc = (xy == 0.0f) ? 1.0f : s / xy;
+  const float sinc = (xy == 0.0f) ? 1.0f : __fdividef(s, xy);
   const float c2xy = c * c - s * s;
+  // A fixed count of A916_TERMS_F32 terms from n0 (>= the window's
+  // n1 - n0 + 1 for every x): every lane of a warp runs the same loop, and
+  // the terms past n1 only widen the window.
   int n0, n1;
   a916_range_f32(x, n0, n1);
   const float q = 0.60653065971f;  // e^{-2h^2}
-  const float nh = n0 * h;
-  const float dm = nh - x, dp = nh + x;
+  float nhn = n0 * h;
+  const float dm = nhn - x, dp = nhn + x;
   float E3 = expf(-(dm * dm));
   float R3 = expf(-(2.0f * h * dm + h * h));
   float E2 = expf(-(dp * dp));
   float R2 = expf(-(2.0f * h * dp + h * h));
   float s23 = 0.0f;
   const float y2 = y * y;
-  for (int n = n0; n <= n1; ++n) {
-    const float nhn = n * h;
+#pragma unroll 4
+  for (int t = 0; t < A916_TERMS_F32; ++t) {
     s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
     E3 *= R3;
     R3 *= q;
     E2 *= R2;
     R2 *= q;
+    nhn += h;
   }
   const float k2h = 0.31830988618f;  // 2h/pi
   float K = ex2 * erfcx_y * c2xy;
