@@ -144,7 +144,13 @@ __global__ void __launch_bounds__(BLOCK)
       const bool full = (ilo <= base) && (ihi >= base + tile_len - 1);
       const double nu0p = L.nu0p, ku = L.ku, a = L.a, a2 = L.a2, Sp = L.Sp;
       const double P1 = Sp * a * INV_SQRTPI;           // GH1: (a/pi) sqrt(pi)
-      const double P3h = 2.0 * (Sp * a * (SQRTPI / 6.0) / PI);  // GH3 outer weight x 2
+      // GH3 as a rational function of r2 alone (u^2 = r2 - a^2):
+      //   (a w1/pi)[4/r2 + 2q/p] = (c3 r2^2 + c45 r2 + c2) / (r2 (r2 (r2 - 3) + C)),
+      // q = r2 + 3/2, p = r2 (r2 - 3) + C, C = 9/4 + 6 a^2, with the line's
+      // factor P3h = 2 a w1 S'/pi in c3 = 3 P3h, c45 = -9/2 P3h, c2 = 2C P3h
+      const double P3h = 2.0 * (Sp * a * (SQRTPI / 6.0) / PI);
+      const double C3 = fma(6.0, a2, 2.25);
+      const double c3 = 3.0 * P3h, c45 = -4.5 * P3h, c2 = 2.0 * C3 * P3h;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (k >= nslot) break;
@@ -157,11 +163,8 @@ __global__ void __launch_bounds__(BLOCK)
             v = P1 * rcp64(r2);
             if (COUNT) cnt[2]++;
           } else if (r2 >= R2_GH3) {
-            // (a w1/pi)[4/r2 + 2q/p], q = r2 + t^2, p = d1 d2 = q^2 - 4t^2u^2
-            const double q = r2 + 1.5;
-            const double p = fma(q, q, (u * u) * -6.0);
-            const double num = fma(2.0, p, r2 * q);
-            v = P3h * (num * rcp64(r2 * p));
+            const double p = fma(r2, r2 - 3.0, C3);
+            v = fma(r2, fma(c3, r2, c45), c2) * rcp64(r2 * p);
             if (COUNT) cnt[1]++;
           } else {
             v = Sp * k916_f64(fabs(u), a, L.erfcx_a, L.sig1);
