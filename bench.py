@@ -143,11 +143,24 @@ class Clocks:
                 "samples": len(rows)}
 
 
+# The Voigt kernels' translation unit: the kernel file and the headers of
+# csrc/ it includes; the profile summaries record a hash of these sources.
+KERNEL_HEADERS = ("voigt_core.cuh", "voigt_common.cuh", "helk_internal.cuh")
+
+
+def kernel_source_hash(kernel_src):
+    d = os.path.dirname(kernel_src)
+    h = hashlib.sha256()
+    for f in (kernel_src,) + tuple(os.path.join(d, x) for x in KERNEL_HEADERS):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(kernel_src, profile_txt):
-    """Per-launch DRAM bytes recorded by an ncu capture, if the kernel source
-    is unchanged since (hash recorded in the summary)."""
+    """Per-launch DRAM bytes recorded by an ncu capture, if the kernel's
+    sources are unchanged since (hash recorded in the summary)."""
     try:
-        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash(kernel_src)
         vals = {}
         with open(profile_txt) as f:
             for line in f:
