@@ -90,18 +90,32 @@ static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y
   const float dm = nhn - x, dp = nhn + x;
   float E3 = expf(-(dm * dm));
   float R3 = expf(-(2.0f * h * dm + h * h));
-  float E2 = expf(-(dp * dp));
-  float R2 = expf(-(2.0f * h * dp + h * h));
   float s23 = 0.0f;
   const float y2 = y * y;
+  // Beyond x = A916_TAIL_F32 - h every S2 term e^{-(nh+x)^2}, n >= 1, is
+  // below e^{-18.49} (outside the window): when that holds for all the
+  // warp's active lanes, the S2 recurrence is left out (a warp-uniform
+  // choice, so the lanes stay in lockstep).
+  if (__all_sync(__activemask(), x > A916_TAIL_F32 - h)) {
 #pragma unroll 4
-  for (int t = 0; t < A916_TERMS_F32; ++t) {
-    s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
-    E3 *= R3;
-    R3 *= q;
-    E2 *= R2;
-    R2 *= q;
-    nhn += h;
+    for (int t = 0; t < A916_TERMS_F32; ++t) {
+      s23 += __fdividef(E3, fmaf(nhn, nhn, y2));
+      E3 *= R3;
+      R3 *= q;
+      nhn += h;
+    }
+  } else {
+    float E2 = expf(-(dp * dp));
+    float R2 = expf(-(2.0f * h * dp + h * h));
+#pragma unroll 4
+    for (int t = 0; t < A916_TERMS_F32; ++t) {
+      s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
+      E3 *= R3;
+      R3 *= q;
+      E2 *= R2;
+      R2 *= q;
+      nhn += h;
+    }
   }
   const float k2h = 0.31830988618f;  // 2h/pi
   float K = ex2 * erfcx_y * c2xy;
