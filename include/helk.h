@@ -240,6 +240,13 @@ int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max);
  * grouping). */
 helk_status helk_set_tile(helk_ctx *ctx, int32_t precision, int64_t n, int32_t tile);
 
+/* Number of CUDA kernels the context has launched since it was created
+ * (tracing: a caller can bracket a region with two calls).  Launches that a
+ * replayed CUDA graph makes (helk_opacity_batch after its first call with
+ * given sizes) are counted when the graph is captured, not at each replay.
+ * Host-only; returns -1 for ctx == NULL. */
+int64_t helk_launch_count(const helk_ctx *ctx);
+
 /* Stage timing (tracing).  With profiling on, the library records a CUDA
  * event pair on the context stream around each stage it launches:
  *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.5)

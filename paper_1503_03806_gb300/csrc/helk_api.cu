@@ -865,6 +865,8 @@ helk_status helk_surrogate_validate(helk_ctx *c, int32_t nx, int32_t ny, int32_t
   return HELK_OK;
 }
 
+int64_t helk_launch_count(const helk_ctx *c) { return c ? c->launches : -1; }
+
 int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max) {
   if (!out || (precision != HELK_PREC_F64 && precision != HELK_PREC_F32_KAHAN)) return 0;
   int cand[16];

@@ -127,6 +127,7 @@ struct helk_ctx {
   int64_t lines_cap = 0;
   // per-call scratch
   helk::LineRec64 *rec64 = nullptr;
+  int64_t launches = 0;  // kernels this context has launched (for tracing)
   helk::LineRec32 *rec32 = nullptr;
   int2 *core_rng = nullptr;  // FP32 form: each line's core points [x, y] (x > y: none)
   int64_t core_cap = 0;

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
 }
 
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
+  ++c->launches;
   k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv);
   return cudaGetLastError();
 }
@@ -586,9 +587,11 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
     cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    ++c->launches;
     k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, nullptr,
                                                            nullptr, coef, mean, kg_out);
   } else {
+    ++c->launches;
     k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, c->sort_a,
                                                         c->sort_b, coef, mean, kg_out);
   }
@@ -656,6 +659,7 @@ cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double
                                 double *direct, double *fit) {
   if (sorted && direct) {
     dim3 grid(nbins, std::min(nm, 64));
+    ++c->launches;
     k_trans_direct<<<grid, TR_THREADS, 0, c->stream>>>(sorted, nb, nm, m_dev, direct);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -667,6 +671,7 @@ cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double
       if (e != cudaSuccess) return e;
     }
     dim3 grid(nbins, (nm + TR_THREADS - 1) / TR_THREADS);
+    ++c->launches;
     k_trans_fit<<<grid, TR_THREADS, smem, c->stream>>>(coef, ncheb, ng, nm, m_dev, fit);
     return cudaGetLastError();
   }

@@ -55,6 +55,7 @@ cudaError_t launch_validate_lines(helk_ctx *c, int64_t n) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
   if (blocks > c->num_sms * 8) blocks = c->num_sms * 8;
+  ++c->launches;
   k_validate<<<blocks, 256, 0, c->stream>>>(n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair,
                                             c->has_gself ? c->gself : nullptr,
                                             c->has_ncoll ? c->ncoll : nullptr,
@@ -208,11 +209,15 @@ cudaError_t launch_sort_lines(helk_ctx *c, int64_t n) {
   double *dtmp = (double *)p;
   int gb = (int)((n + 255) / 256);
   if (gb > c->num_sms * 16) gb = c->num_sms * 16;
+  ++c->launches;
   k_line_keys<<<gb, 256, 0, c->stream>>>(n, c->nu0, ka, va);
   for (int pass = 0; pass < 8; ++pass) {
     int shift = pass * 8;
+    ++c->launches;
     k_rs_upsweep<<<nblk, RS_THREADS, 0, c->stream>>>(ka, n, shift, counts, nblk);
+    ++c->launches;
     k_rs_scan<<<1, 1024, 0, c->stream>>>(counts, (int64_t)256 * nblk);
+    ++c->launches;
     k_rs_downsweep<<<nblk, RS_THREADS, 0, c->stream>>>(ka, va, kb, vb, n, shift, counts, nblk);
     unsigned long long *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
@@ -223,6 +228,7 @@ cudaError_t launch_sort_lines(helk_ctx *c, int64_t n) {
                        c->has_weight ? c->lweight : nullptr};
   for (int f = 0; f < 9; ++f) {
     if (!fields[f]) continue;
+    ++c->launches;
     k_gather<<<gb, 256, 0, c->stream>>>(n, va, fields[f], dtmp);
     cudaError_t e = cudaMemcpyAsync(fields[f], dtmp, n * 8, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
@@ -370,6 +376,7 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
   PrepArgs A{mass, cut.kind, cut.value, cut.cap, g.nu_min, g.dnu, g.n};
   const CondArgs one = single ? *single : CondArgs{0, 0, 0, 0};
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
+  ++c->launches;
   k_lineprep<<<grid, 256, 0, c->stream>>>(
       n, c->nu0, c->S0, c->has_E ? c->El : nullptr, c->gair, c->has_gself ? c->gself : nullptr,
       c->has_ncoll ? c->ncoll : nullptr, c->has_delta ? c->delta : nullptr,
@@ -451,6 +458,7 @@ cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   const int64_t n = c->nlines;
   if (n <= 0) return cudaSuccess;
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
+  ++c->launches;
   k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->ckey, c->cstats, c->rec32,
                                         c->core_rng);
   return cudaGetLastError();
@@ -490,6 +498,7 @@ __global__ void k_tilemap(int64_t nlines, const double *__restrict__ ckey, int64
 
 cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile, int64_t ntiles) {
   dim3 grid((unsigned)((ntiles + 7) / 8), n_cond);  // 8 warps, one tile each
+  ++c->launches;
   k_tilemap<<<grid, 256, 0, c->stream>>>(c->nlines, c->ckey, g.n, tile, ntiles, c->cstats,
                                          c->tile_lo, c->tile_hi);
   return cudaGetLastError();
@@ -512,6 +521,7 @@ __global__ void k_cond_order(int n_cond, const CondStats *__restrict__ cst, int 
 }
 
 cudaError_t launch_cond_order(helk_ctx *c, int n_cond) {
+  ++c->launches;
   k_cond_order<<<1, 32, 0, c->stream>>>(n_cond, c->cstats, c->cond_order);
   return cudaGetLastError();
 }

@@ -578,6 +578,7 @@ cudaError_t launch_mlp_validate(helk_ctx *c, int nx, int ny, int per, double *er
   int64_t blocks = (n + 127) / 128;
   if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
   unsigned int *cnt = reinterpret_cast<unsigned int *>(err_dev + (int64_t)nx * ny);
+  ++c->launches;
   k_mlp_validate<<<(unsigned)blocks, 256, smem, c->stream>>>(
       c->mlp_p, nx, ny, per, reinterpret_cast<unsigned long long *>(err_dev), cnt);
   return cudaGetLastError();
@@ -591,6 +592,7 @@ cudaError_t launch_mlp_queue(helk_ctx *c, int n_cond, int64_t ngrid, double weig
   int64_t blocks = (c->squeue_cap + 127) / 128;
   if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
   if (blocks < 1) blocks = 1;
+  ++c->launches;
   k_mlp_queue<<<(unsigned)blocks, 256, smem, c->stream>>>(c->mlp_p, c->squeue, ngrid, weight, c->cstats, kappa);
   return cudaGetLastError();
 }
@@ -606,6 +608,7 @@ cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const d
   if (e != cudaSuccess) return e;
   int64_t blocks = (n + 127) / 128;
   if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
+  ++c->launches;
   k_mlp_eval<<<(unsigned)blocks, 256, smem, c->stream>>>(params, n, x, y, k);
   return cudaGetLastError();
 }
@@ -615,6 +618,7 @@ cudaError_t launch_mlp_train_step(helk_ctx *c, const float *params, const float 
   const size_t smem = sizeof(TrainSmem);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  ++c->launches;
   k_mlp_train<<<(unsigned)((B + 127) / 128), 256, smem, c->stream>>>(params, feat, tgt, b0, B, grads, loss);
   return cudaGetLastError();
 }
@@ -622,6 +626,7 @@ cudaError_t launch_mlp_train_step(helk_ctx *c, const float *params, const float 
 cudaError_t launch_mlp_adam(helk_ctx *c, float *p, float *m, float *v, const float *grad, float lr, int step) {
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  ++c->launches;
   k_mlp_adam<<<34, 256, 0, c->stream>>>(p, m, v, grad, MLP_NPARAMS, lr, b1, b2, 1e-8f, c1, c2);
   return cudaGetLastError();
 }
@@ -630,6 +635,7 @@ cudaError_t launch_mlp_samples(helk_ctx *c, int64_t n, uint64_t seed, float *fea
                                double *ys) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  ++c->launches;
   k_mlp_samples<<<(unsigned)blocks, 256, 0, c->stream>>>(n, seed, feat, tgt, xs, ys);
   return cudaGetLastError();
 }
@@ -637,6 +643,7 @@ cudaError_t launch_mlp_samples(helk_ctx *c, int64_t n, uint64_t seed, float *fea
 cudaError_t launch_a916_points(helk_ctx *c, int64_t n, const double *x, const double *y, double *k) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
+  ++c->launches;
   k_a916_points<<<(unsigned)blocks, 256, 0, c->stream>>>(n, x, y, k);
   return cudaGetLastError();
 }

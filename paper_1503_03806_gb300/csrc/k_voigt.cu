@@ -521,6 +521,7 @@ __global__ void __launch_bounds__(CORE_BLOCK)
   const int64_t last = warp_search(ckey, first, nlines, (double)(B - 1) + W, true);
   const LineRec32 *rec = rec_all + (int64_t)cond * nlines;
   const int2 *core = core_all + (int64_t)cond * nlines;
+  const double scale = ldexp(weight, cst[cond].scale_exp);  // as k_voigt_f32's flush
   const int i = (int)(A + (threadIdx.x & 31));
   float v = 0.0f;
   unsigned long long n916 = 0, nterm = 0;
@@ -539,8 +540,7 @@ __global__ void __launch_bounds__(CORE_BLOCK)
         nterm += (unsigned long long)(n1 - n0 + 1);
       }
     }
-    if (v != 0.0f)
-      kappa_all[(int64_t)cond * ngrid + i] += ldexp(weight, cst[cond].scale_exp) * (double)v;
+    if (v != 0.0f) kappa_all[(int64_t)cond * ngrid + i] += scale * (double)v;
   }
   if (COUNT) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -558,6 +558,7 @@ cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const
   if (o.precision != HELK_PREC_F32_KAHAN || c->nlines <= 0) return cudaSuccess;
   SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
   const dim3 grid((unsigned)((g.n + CORE_BLOCK - 1) / CORE_BLOCK), (unsigned)n_cond);
+  ++c->launches;
   if (o.count_regions)
     k_core_f32<true><<<grid, CORE_BLOCK, 0, c->stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey, (int)g.n,
                                                           o.weight, kappa, c->cstats, sq);
@@ -633,6 +634,7 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
     if (o.count_regions) {
       if (ns != F32_COUNT_NSLOT) return cudaErrorInvalidValue;
       auto kern = k_voigt_f32<F32_BLOCK, F32_COUNT_NSLOT, F32_LCH, true, 3>;
+      ++c->launches;
       kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(
           c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, o.weight,
           o.accumulate, kappa, c->cstats, c->stats, sq);
@@ -641,6 +643,7 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
 #define X(NS, MB)                                                                                 \
     if (ns == NS) {                                                                               \
       auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false, MB>;                                  \
+      ++c->launches;                                                                               \
       kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(              \
           c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n,    \
           o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                                 \

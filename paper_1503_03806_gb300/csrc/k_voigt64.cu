@@ -213,6 +213,7 @@ __global__ void k_selftest_timeout(DevStats *st, long long polls) {
 }
 
 cudaError_t launch_selftest_timeout(helk_ctx *c, int polls) {
+  ++c->launches;
   k_selftest_timeout<<<1, 32, 0, c->stream>>>(c->stats, polls);
   return cudaGetLastError();
 }
@@ -262,11 +263,13 @@ cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const 
   const int nslot = tile_len / F64_BLOCK;
   if (o.count_regions) {
     auto kern = k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true>;
+    ++c->launches;
     kern<<<persistent_grid(c, kern, F64_BLOCK, nitems), F64_BLOCK, 0, c->stream>>>(
         c->rec64, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, g.nu_min, g.dnu,
         (int)g.n, nslot, o.weight, o.accumulate, kappa, c->cstats, c->stats);
   } else {
     auto kern = k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false>;
+    ++c->launches;
     kern<<<persistent_grid(c, kern, F64_BLOCK, nitems), F64_BLOCK, 0, c->stream>>>(
         c->rec64, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, g.nu_min, g.dnu,
         (int)g.n, nslot, o.weight, o.accumulate, kappa, c->cstats, c->stats);

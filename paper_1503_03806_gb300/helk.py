@@ -85,6 +85,7 @@ SIGNATURES = [
                                      ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
                                      ctypes.POINTER(_I32)]),
     ("helk_tile_candidates", _I32, [_I32, _P, _I32]),
+    ("helk_launch_count", _I64, [_P]),
     ("helk_set_tile", ctypes.c_int, [_P, _I32, _I64, _I32]),
 ]
 HELK_NSTAGES = 4
@@ -330,6 +331,10 @@ class Context:
         _check(self.h, lib.helk_autotune(self.h, float(T), float(P), float(mass), ctypes.byref(_cut(cut)),
                                          ctypes.byref(g), ctypes.byref(o), ctypes.byref(t)))
         return int(t.value)
+
+    def launch_count(self):
+        """Kernels this context has launched so far."""
+        return int(lib.helk_launch_count(self.h))
 
     def set_tile(self, precision, n, tile):
         """Fix the Voigt tile shape for grids of n points (0: built-in choice)."""
