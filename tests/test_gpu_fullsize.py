@@ -1,0 +1,126 @@
+"""Parity at the full sizes of the larger workloads, in the launch
+configurations the benchmark times, on sampled grid points the oracle
+computes one by one.
+
+- tp_grid: 1e6 lines (log-normal strengths, lower-state energies), all
+  8 T x 8 P conditions in one graph-captured FP32 batch with an autotuned
+  tile, and an FP64 batch of 8 of them; sampled points of several
+  conditions against the oracle (FP64: 1e-9; FP32: 1e-5 where kappa exceeds
+  1e-8 of its bin maximum).
+- mixed: 4 species x 2.5e7 lines (masses 18, 16, 44, 17 amu, mixing 1/4
+  each) in one upload with per-line mass and abundance weight, on the 3e7
+  point grid at 0.001 cm^-1; one condition in the FP32 form.
+
+The oracle sums every line of the list whose window holds the point.  For
+the 1e8-line list it is given, per sampled region, the lines whose centre
+lies within the largest possible window half-width (the 100 cm^-1 cap plus
+a grid step) of the region: no other line can reach those points, so its
+sums are the full list's.  The bin maxima that select the FP32 points come
+from the GPU result; the expected values come from the oracle only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_03806_gb300 import synth
+from tests.helpers import Case, assert_rel
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-9
+RTOL32 = 1e-5
+FLOOR = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_03806_gb300 import build
+    build.build()
+    from paper_1503_03806_gb300 import helk
+    c = helk.Context(0)
+    yield c
+    c.close()
+
+
+def _selected(k_gpu_row, nbins, idx):
+    """Points whose kappa exceeds FLOOR of their bin maximum."""
+    nb = k_gpu_row.shape[0] // nbins
+    bmax = k_gpu_row.reshape(nbins, nb).max(axis=1)
+    return k_gpu_row[idx] > FLOOR * bmax[idx // nb]
+
+
+def _sample_idx(ngrid, seed, n=120):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([rng.integers(0, ngrid, n), [0, ngrid - 1]]))
+
+
+def test_tp_grid_batches(ctx):
+    import torch
+    from paper_1503_03806_gb300 import helk
+    w = synth.WORKLOADS["tp_grid"]
+    lines = synth.workload_lines("tp_grid")
+    Ts = np.repeat(np.asarray(w["T"]), len(w["P_atm"]))
+    Ps = np.tile(np.asarray(w["P_atm"]), len(w["T"]))
+    qs = (296.0 / Ts) ** 1.5
+    grid = (w["nu_min"], w["dnu"], w["ngrid"])
+    ctx.upload(lines)
+    ctx.autotune(Ts[0], Ps[-1], w["mass"], w["cut"], grid, precision=helk.HELK_PREC_F32_KAHAN, q_ratio=qs[0])
+    kb = torch.empty((len(Ts), grid[2]), dtype=torch.float64, device="cuda")
+    ctx.opacity_batch(Ts, Ps, w["mass"], w["cut"], grid, out=kb, precision=helk.HELK_PREC_F32_KAHAN,
+                      q_ratio=qs)
+    ctx.opacity_batch(Ts, Ps, w["mass"], w["cut"], grid, out=kb, precision=helk.HELK_PREC_F32_KAHAN,
+                      q_ratio=qs)  # a replay of the captured graph
+    k32 = kb.cpu().numpy()
+    sub = np.array([0, 9, 27, 36, 54, 63])  # cold/hot x low/high pressure
+    k64 = ctx.opacity_batch(Ts[sub], Ps[sub], w["mass"], w["cut"], grid, precision=helk.HELK_PREC_F64,
+                            q_ratio=qs[sub]).cpu().numpy()
+    idx = _sample_idx(grid[2], 31)
+    for j, c in enumerate(sub):
+        case = Case(Ts[c], Ps[c], w["mass"], grid, w["cut"], q_ratio=qs[c])
+        ko, _ = oracle.opacity_points(lines, case.oracle_cond(), idx)
+        assert_rel(k64[j][idx], ko, RTOL64, "tp_grid FP64 condition %d" % c)
+        sel = _selected(k32[c], w["nbins"], idx)
+        assert sel.sum() > 0
+        err = np.abs(k32[c][idx][sel] - ko[sel]) / ko[sel]
+        assert err.max() <= RTOL32, ("tp_grid FP32 condition %d" % c, err.max())
+
+
+def test_mixed_species_full_size(ctx):
+    import torch
+    from paper_1503_03806_gb300 import helk
+    w = synth.WORKLOADS["mixed"]
+    parts = []
+    for s, (m, x) in enumerate(zip(w["species_mass"], w["mixing"])):
+        L = synth.workload_lines("mixed", species=s)
+        L["mass"] = np.full(L["nu0"].shape[0], m)
+        L["weight"] = np.full(L["nu0"].shape[0], x)
+        parts.append(L)
+    lines = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    del parts
+    order = np.argsort(lines["nu0"], kind="stable")
+    lines = {k: np.ascontiguousarray(v[order]) for k, v in lines.items()}
+    del order
+    grid = (w["nu_min"], w["dnu"], w["ngrid"])
+    T, P = w["T"][2], w["P_atm"][2]
+    case = Case(T, P, 18.0, grid, w["cut"], q_ratio=(296.0 / T) ** 1.5)
+    ctx.upload(lines)
+    k = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN).cpu().numpy()
+    assert np.all(np.isfinite(k)) and k.max() > 0
+    # three regions of 40 points; the oracle gets every line that can reach them
+    rng = np.random.default_rng(5)
+    reach = w["cut"][2] + grid[1]
+    for lo in (1000.0, 14000.0, 29000.0):
+        i0 = int((lo - grid[0]) / grid[1])
+        idx = np.sort(rng.choice(np.arange(i0, i0 + 200_000), 40, replace=False))
+        nu_a, nu_b = grid[0] + idx[0] * grid[1], grid[0] + idx[-1] * grid[1]
+        a, b = np.searchsorted(lines["nu0"], [nu_a - reach, nu_b + reach])
+        near = {kk: np.ascontiguousarray(v[a:b]) for kk, v in lines.items()}
+        ko, _ = oracle.opacity_points(near, case.oracle_cond(), idx)
+        sel = _selected(k, w["nbins"], idx)
+        assert sel.sum() > 0
+        err = np.abs(k[idx][sel] - ko[sel]) / ko[sel]
+        assert err.max() <= RTOL32, (lo, err.max())
+    del lines
+    torch.cuda.empty_cache()

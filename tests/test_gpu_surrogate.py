@@ -147,3 +147,31 @@ def test_surrogate_form_beats_fp64_form(ctx, trained):
     print("core-dominated opacity: FP64 %.3f ms, FP32 %.3f ms, FP32+surrogate %.3f ms"
           % (t64 * 1e3, t32 * 1e3, ts * 1e3))
     assert ts < t64
+
+
+def test_full_size_surrogate_workload(ctx, trained):
+    # the 1e7-line workload (log-normal strengths, lower-state energies) at
+    # 1500 K, 1 atm on the 3e6-point grid, FP32 with the surrogate routed;
+    # sampled regions against the oracle, which gets every line whose window
+    # can reach them (centre within the 100 cm^-1 cap plus a grid step)
+    from paper_1503_03806_gb300 import helk
+    w = synth.WORKLOADS["surrogate"]
+    lines = synth.workload_lines("surrogate")
+    grid = (w["nu_min"], w["dnu"], w["ngrid"])
+    case = Case(w["T"][0], w["P_atm"][0], w["mass"], grid, w["cut"], q_ratio=(296.0 / w["T"][0]) ** 1.5)
+    ctx.upload(lines)
+    k = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN, surrogate=True).cpu().numpy()
+    nb = w["ngrid"] // w["nbins"]
+    bmax = k.reshape(w["nbins"], nb).max(axis=1)
+    rng = np.random.default_rng(12)
+    reach = w["cut"][2] + grid[1]
+    for lo in (2000.0, 15000.0, 28000.0):
+        i0 = int((lo - grid[0]) / grid[1])
+        idx = np.sort(rng.choice(np.arange(i0, i0 + 20_000), 60, replace=False))
+        a, b = np.searchsorted(lines["nu0"], [grid[0] + idx[0] * grid[1] - reach,
+                                              grid[0] + idx[-1] * grid[1] + reach])
+        near = {kk: np.ascontiguousarray(v[a:b]) for kk, v in lines.items()}
+        ko, _ = oracle.opacity_points(near, case.oracle_cond(), idx)
+        sel = k[idx] > 1e-8 * bmax[idx // nb]
+        assert sel.sum() > 0
+        assert np.max(np.abs(k[idx][sel] / ko[sel] - 1)) < 1e-4, lo
