@@ -145,7 +145,7 @@ void helk_destroy(helk_ctx *c) {
                   (void *)c->squeue, c->squeue_buf})
     if (p) cudaFree(p);
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
-                  c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->tile_lo, c->tile_hi,
+                  c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->ckey32, c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
                   c->mean_dev, c->tmp};
   for (void *p : bufs)
@@ -159,6 +159,10 @@ void helk_destroy(helk_ctx *c) {
   if (c->cond_ev) cudaEventDestroy(c->cond_ev);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->kcore) cudaFree(c->kcore);
   for (int st = 0; st < HELK_NSTAGES; ++st)
     for (cudaEvent_t e : c->ev[st]) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
@@ -320,7 +324,8 @@ static helk_status ensure_conds(helk_ctx *c, int n_cond) {
 }
 
 // Buffers for n_cond conditions of the current line list and tile shape.
-static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts &o, int64_t ntiles) {
+static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts &o, int64_t ntiles,
+                                       int64_t ngrid) {
   const int64_t nl = std::max<int64_t>(c->nlines, 1) * n_cond;
   HELK_TRY(ensure_conds(c, n_cond));
   HELK_TRY(ensure_buf(c, (void **)&c->rec64, &c->rec_cap, nl * (int64_t)sizeof(LineRec64), "line records"));
@@ -329,6 +334,15 @@ static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts 
     HELK_TRY(ensure_buf(c, (void **)&c->rec32, &c->rec32_cap, nl * (int64_t)sizeof(LineRec32),
                         "FP32 line records"));
     HELK_TRY(ensure_buf(c, (void **)&c->core_rng, &c->core_cap, nl * (int64_t)sizeof(int2), "line cores"));
+    HELK_TRY(ensure_buf(c, (void **)&c->ckey32, &c->ckey32_cap, std::max<int64_t>(c->nlines, 1) * 4,
+                        "line keys"));
+    HELK_TRY(ensure_buf(c, (void **)&c->kcore, &c->kcore_cap, ngrid * n_cond * 4, "core sums"));
+    if (!c->side_stream)
+      HELK_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking), "core stream"));
+    if (!c->fork_ev)
+      HELK_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming), "core stream"));
+    if (!c->join_ev)
+      HELK_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming), "core stream"));
   }
   HELK_TRY(ensure_tiles(c, ntiles * n_cond));
   if (o.surrogate && !c->squeue) {
@@ -380,8 +394,20 @@ static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const 
                       "voigt"));
   if (o.surrogate)
     HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->squeue->count, 0, sizeof(unsigned long long), c->stream), "voigt"));
-  HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
-  HELK_TRY(cuda_check(c, launch_voigt_core(c, n_cond, *g, o, kappa), "voigt cores"));
+  if (o.precision == HELK_PREC_F32_KAHAN) {
+    // The Algorithm 916 cores run on the side stream beside the main kernel
+    // (whose CTAs are issued first and leave registers and warp slots on every
+    // SM), into their own buffer; their sums are added once both are done.
+    HELK_TRY(cuda_check(c, cudaEventRecord(c->fork_ev, c->stream), "voigt"));
+    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+    HELK_TRY(cuda_check(c, cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0), "voigt cores"));
+    HELK_TRY(cuda_check(c, launch_voigt_core(c, n_cond, *g, o), "voigt cores"));
+    HELK_TRY(cuda_check(c, cudaEventRecord(c->join_ev, c->side_stream), "voigt cores"));
+    HELK_TRY(cuda_check(c, cudaStreamWaitEvent(c->stream, c->join_ev, 0), "voigt cores"));
+    HELK_TRY(cuda_check(c, launch_core_add(c, n_cond, *g, o, kappa), "voigt cores"));
+  } else {
+    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+  }
   if (o.surrogate) HELK_TRY(cuda_check(c, launch_mlp_queue(c, n_cond, g->n, o.weight, kappa), "surrogate"));
   return HELK_OK;
 }
@@ -401,7 +427,7 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   }
   const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
   const int64_t ntiles = (g->n + tile - 1) / tile;
-  HELK_TRY(ensure_call_buffers(c, 1, o, ntiles));
+  HELK_TRY(ensure_call_buffers(c, 1, o, ntiles, g->n));
   const CondArgs one{T, P, o.q_ratio, 0.0};
   stage_begin(c, HELK_STAGE_LINEPREP);
   HELK_TRY(prepare_lines(c, 1, &one, mass, cut, g, o));
@@ -437,7 +463,7 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   const int ncand = voigt_tile_candidates(o.precision, cand, 16);
   int64_t max_tiles = 0;
   for (int i = 0; i < ncand; ++i) max_tiles = std::max(max_tiles, (g->n + cand[i] - 1) / cand[i]);
-  HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles));
+  HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles, g->n));
   const CondArgs one{T, P, o.q_ratio, 0.0};
   HELK_TRY(prepare_lines(c, 1, &one, mass, cut, g, o));
   cudaEvent_t e0, e1;
@@ -483,11 +509,11 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
 static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const helk_cutoff *cut,
                              const helk_grid *g, const helk_opts &o, const double *kappa, int tile) {
   char b[512];
-  snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%d|%p|%d|%p|%p|%p|%p|%p", n_cond,
+  snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%d|%p|%d|%p|%p|%p|%p|%p|%p", n_cond,
            (long long)c->nlines, (const void *)c->nu0, mass, cut->kind, cut->value, cut->cap, g->nu_min,
            g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions, o.surrogate,
            (const void *)kappa, tile, (const void *)c->rec64, (const void *)c->rec32,
-           (const void *)c->tile_lo, (const void *)c->cstats, (const void *)c->squeue);
+           (const void *)c->tile_lo, (const void *)c->cstats, (const void *)c->squeue, (const void *)c->kcore);
   return std::string(b);
 }
 
@@ -522,7 +548,7 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
   }
   const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
   const int64_t ntiles = (g->n + tile - 1) / tile;
-  HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles));
+  HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles, g->n));
   if (!c->cap_stream)
     HELK_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "graph stream"));
   if (!c->cond_ev) HELK_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->cond_ev, cudaEventDisableTiming), "graph"));
@@ -612,7 +638,7 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
   }
   HELK_TRY(bind_device(c));
   if (c->pinv_nb != nb || c->pinv_ncheb != ncheb || !c->pinv) {
-    HELK_TRY(ensure_buf(c, (void **)&c->pinv, &c->pinv_cap, nb * ncheb * 8, "kdist pseudo-inverse"));
+    HELK_TRY(ensure_buf(c, (void **)&c->pinv, &c->pinv_cap, pinv_bytes(nb, ncheb), "kdist pseudo-inverse"));
     HELK_TRY(ensure_buf(c, &c->tmp, &c->tmp_cap, nb * ncheb * 8, "kdist pseudo-inverse"));
     stage_begin(c, HELK_STAGE_SETUP);
     HELK_TRY(cuda_check(c, launch_pinv(c, nb, ncheb, (double *)c->tmp), "kdist pseudo-inverse"));

@@ -133,6 +133,14 @@ struct helk_ctx {
   int64_t core_cap = 0;
   double *ckey = nullptr;
   int64_t ckey_cap = 0;
+  int32_t *ckey32 = nullptr;  // FP32 form: ckey clamped to +-2e9 (order kept), for integer searches
+  int64_t ckey32_cap = 0;
+  // FP32 form: the core kernel runs on side_stream beside the main Voigt
+  // kernel and leaves its per-point sums in kcore (FP32, n_cond x n points)
+  float *kcore = nullptr;
+  int64_t kcore_cap = 0;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t rec_cap = 0, rec32_cap = 0;
   int32_t *tile_lo = nullptr, *tile_hi = nullptr;
   int64_t tile_cap = 0;
@@ -277,7 +285,8 @@ cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk
                          double *kappa, int tile_len, int64_t ntiles);
 // FP32 form: the Algorithm 916 cores that k_voigt_f32 leaves out, added into
 // kappa (launched after launch_voigt; no-op for the FP64 form).
-cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa);
+cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o);
+cudaError_t launch_core_add(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa);
 // k_voigt64.cu: the FP64 form (called by the dispatch above) and the
 // bounded-wait self-test
 int f64_tile_candidates(int *out, int max);
@@ -286,6 +295,7 @@ cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const 
                              int tile_len, int64_t ntiles);
 cudaError_t launch_selftest_timeout(helk_ctx *c, int polls);
 // k_kdist.cu
+int64_t pinv_bytes(int64_t nb, int ncheb);
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
                               double kappa_floor, double *coef, double *mean, double *kg_out);

@@ -28,6 +28,7 @@ namespace helk {
 constexpr int KD_THREADS = 512;
 constexpr int KD_WARPS = KD_THREADS / 32;
 constexpr int NCHEB_MAX = 32;
+constexpr int KD_LNTAB = 256;  // float2 entries: ln c_j, then 1/c_j
 
 __device__ __forceinline__ uint32_t lanemask_lt_kd() {
   uint32_t m;
@@ -130,7 +131,7 @@ __device__ double block_sum_pi(double v, double *red) {
 }
 
 __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, double *work,
-                                                     double *vtv_out, double *P) {
+                                                     double *vtv_out, double *P, float2 *lntab) {
   __shared__ double red[PI_THREADS / 32];
   __shared__ double R[NCHEB_MAX * NCHEB_MAX];
   __shared__ double vtv[NCHEB_MAX];
@@ -222,11 +223,27 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
   float2 *Ps = reinterpret_cast<float2 *>(P);
   for (int64_t e = tid; e < (int64_t)ncheb * nh; e += PI_THREADS) Ps[e] = W[e];
   if (tid == 0 && vtv_out) vtv_out[0] = vtv[0];
+  // the logarithm's table, ln c_j and 1/c_j (c_j = 1 + j/128) as FP32
+  // (high, low) pairs, computed here once instead of in every bin's CTA
+  if (tid < 128) {
+    const double cj = 1.0 + tid / 128.0, l = log(cj), ic = 1.0 / cj;
+    const float lh = (float)l, ih = (float)ic;
+    lntab[tid] = make_float2(lh, (float)(l - (double)lh));
+    lntab[128 + tid] = make_float2(ih, (float)(ic - (double)ih));
+  }
+}
+
+// The pseudo-inverse buffer: nb ncheb doubles of work space (the
+// symmetrized half of P at its front when done), then the logarithm's table.
+int64_t pinv_bytes(int64_t nb, int ncheb) { return (nb * ncheb + KD_LNTAB) * 8; }
+
+static float2 *pinv_lntab(helk_ctx *c, int64_t nb, int ncheb) {
+  return reinterpret_cast<float2 *>(c->pinv + nb * ncheb);
 }
 
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
   ++c->launches;
-  k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv);
+  k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv, pinv_lntab(c, nb, ncheb));
   return cudaGetLastError();
 }
 
@@ -452,19 +469,79 @@ __device__ __forceinline__ void dfma_acc(float &sh, float &sl, float2 P, float2 
   sl += err + (e + fmaf(P.x, L.y, P.y * L.x));
 }
 
+// The bin sum in 128-bit unsigned fixed point (lo, hi), exactly: a value
+// m 2^(e - 1075) (m < 2^53, e the biased exponent, 1 for subnormals) is
+// added as m 2^(e - emax + fxb), where emax is the largest value's exponent
+// and fxb = 74 - ceil(log2 N_b), so N_b terms stay below 2^127.  Terms of a
+// negative exponent are truncated (each below 2^-(fxb + 52) of the largest
+// value).  Integer operations only.
+__device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long long &hi, unsigned long long kb,
+                                       int emax, int fxb) {
+  const int e = (int)(kb >> 52);
+  const unsigned long long m = (kb & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int sh = max(e, 1) - emax + fxb;
+  unsigned long long tl = 0, th = 0;
+  if (sh >= 64) {
+    th = m << (sh - 64);
+  } else if (sh > 0) {
+    tl = m << sh;
+    th = m >> (64 - sh);
+  } else if (sh > -53) {
+    tl = m >> -sh;
+  }
+  lo += tl;
+  hi += th + (lo < tl);
+}
+
+__device__ __forceinline__ void fx_warp_sum(unsigned long long &lo, unsigned long long &hi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    lo += l2;
+    hi += h2 + (lo < l2);
+  }
+}
+
+__device__ __forceinline__ float2 shfl_xor_f2(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// Warp sums of eight float-float values by reduce-scatter: each exchange
+// halves the values a lane carries, so lane l ends with the warp's sum of
+// value l >> 2 (18 shuffle pairs instead of 40 for eight plain reductions).
+__device__ __forceinline__ float2 ff_warp_sum8(const float2 (&v)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float2 v4[4], v2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 keep = b4 ? v[i + 4] : v[i], send = b4 ? v[i] : v[i + 4];
+    v4[i] = ff_add(keep, shfl_xor_f2(send, 16));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float2 keep = b3 ? v4[i + 2] : v4[i], send = b3 ? v4[i] : v4[i + 2];
+    v2[i] = ff_add(keep, shfl_xor_f2(send, 8));
+  }
+  float2 r = ff_add(b2 ? v2[1] : v2[0], shfl_xor_f2(b2 ? v2[0] : v2[1], 4));
+  r = ff_add(r, shfl_xor_f2(r, 2));
+  return ff_add(r, shfl_xor_f2(r, 1));
+}
+
 // Per-bin sort + fit.  MODE 0: keys in shared memory (nb <= KD_REG_MAX,
 // register-resident passes, one array); MODE 1: keys in the global ping-pong
 // buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
 template <int MODE>
 __global__ void __launch_bounds__(KD_THREADS)
     k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
-                const float2 *__restrict__ P, unsigned long long *gA, unsigned long long *gB,
-                double *__restrict__ coef, double *__restrict__ mean, double *__restrict__ kg_out) {
+                const float2 *__restrict__ P, const float2 *__restrict__ lntab, unsigned long long *gA,
+                unsigned long long *gB, double *__restrict__ coef, double *__restrict__ mean,
+                double *__restrict__ kg_out) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t hist[KD_HIST];
   __shared__ uint32_t wtot[32];
   __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
-  __shared__ double red[KD_WARPS][NCHEB_MAX + 1];
+  __shared__ float2 red[KD_WARPS][NCHEB_MAX];
+  __shared__ unsigned long long red_fx[KD_WARPS][2];
   __shared__ float2 s_lnc[128], s_invc[128];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t off = (int64_t)blockIdx.x * nb;
@@ -476,11 +553,12 @@ __global__ void __launch_bounds__(KD_THREADS)
     vand &= k;
     vor |= k;
   }
-  if (tid < 128) {  // ln c_j and 1/c_j as FP32 (high, low) pairs
-    const double cj = 1.0 + tid / 128.0, l = log(cj), ic = 1.0 / cj;
-    const float lh = (float)l, ih = (float)ic;
-    s_lnc[tid] = make_float2(lh, (float)(l - (double)lh));
-    s_invc[tid] = make_float2(ih, (float)(ic - (double)ih));
+  if (tid < KD_LNTAB) {  // ln c_j and 1/c_j as FP32 (high, low) pairs
+    const float2 t = lntab[tid];
+    if (tid < 128)
+      s_lnc[tid] = t;
+    else
+      s_invc[tid - 128] = t;
   }
   for (int o = 16; o > 0; o >>= 1) {
     vand &= __shfl_down_sync(0xffffffffu, vand, o);
@@ -505,20 +583,24 @@ __global__ void __launch_bounds__(KD_THREADS)
     S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
   }
   // sorted values out, the bin sum, and L_j in place as a split pair
-  double ksum = 0.0;
+  const unsigned long long kmax = S[nb - 1];
+  const int emax = max((int)(kmax >> 52), 1);
+  const int fxb = 74 - (nb > 1 ? 32 - __clz(nb - 1) : 0);
+  unsigned long long fx_lo = 0, fx_hi = 0;
   float2 *Ls = reinterpret_cast<float2 *>(S);
   const unsigned long long floor_bits = (unsigned long long)__double_as_longlong(kappa_floor);
+  __syncthreads();  // every thread has read kmax before L_j overwrites the keys
   for (int j = tid; j < nb; j += KD_THREADS) {
     const unsigned long long kb = S[j];
-    const double kv = __longlong_as_double((long long)kb);
-    if (kg_out) kg_out[off + j] = kv;
-    ksum += kv;
+    if (kg_out) kg_out[off + j] = __longlong_as_double((long long)kb);
+    fx_add(fx_lo, fx_hi, kb, emax, fxb);
     // non-negative doubles order as their bit patterns: max(k, floor) on the bits
     Ls[j] = log_ff(kb > floor_bits ? kb : floor_bits, s_lnc, s_invc);
   }
-  {
-    const double v = warp_sum(ksum);
-    if (lane == 0) red[w][NCHEB_MAX] = v;
+  fx_warp_sum(fx_lo, fx_hi);
+  if (lane == 0) {
+    red_fx[w][0] = fx_lo;
+    red_fx[w][1] = fx_hi;
   }
   __syncthreads();
   // c = P L, eight coefficients per sweep over the first half of the points:
@@ -550,24 +632,34 @@ __global__ void __launch_bounds__(KD_THREADS)
           if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pb[q], (q & 1) ? Lm : Lp);
       }
     }
+    float2 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      if (k0 + q < ncheb) {
-        const double v = warp_sum((double)sh[q] + (double)sl[q]);
-        if (lane == 0) red[w][k0 + q] = v;
-      }
+      float h, l;
+      two_sum_f(sh[q], sl[q], h, l);
+      v[q] = make_float2(h, l);
     }
+    const float2 r = ff_warp_sum8(v, lane);
+    if ((lane & 3) == 0 && k0 + (lane >> 2) < ncheb) red[w][k0 + (lane >> 2)] = r;
   }
   __syncthreads();
   if (tid < ncheb) {
-    double s = 0.0;
-    for (int i = 0; i < KD_WARPS; ++i) s += red[i][tid];
-    coef[(int64_t)blockIdx.x * ncheb + tid] = s;
+    float2 s = red[0][tid];
+    for (int i = 1; i < KD_WARPS; ++i) s = ff_add(s, red[i][tid]);
+    coef[(int64_t)blockIdx.x * ncheb + tid] = (double)s.x + (double)s.y;
   }
   if (tid == NCHEB_MAX && mean) {
-    double s = 0.0;
-    for (int i = 0; i < KD_WARPS; ++i) s += red[i][NCHEB_MAX];
-    mean[blockIdx.x] = s / (double)nb;
+    unsigned long long lo = 0, hi = 0;
+    for (int i = 0; i < KD_WARPS; ++i) {
+      lo += red_fx[i][0];
+      hi += red_fx[i][1] + (lo < red_fx[i][0]);
+    }
+    double m;
+    if ((kmax >> 52) >= 0x7FF)  // infinite or NaN largest value (or a negative one)
+      m = (kmax >> 63) ? __longlong_as_double(0x7FF8000000000000ll) : __longlong_as_double((long long)kmax);
+    else
+      m = ldexp(fma((double)hi, 0x1p64, (double)lo), emax - 1075 - fxb) / (double)nb;
+    mean[blockIdx.x] = m;
   }
 }
 
@@ -582,18 +674,19 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
                               double kappa_floor, double *coef, double *mean, double *kg_out) {
   const int nb = (int)(n / nbins);
   const float2 *P = reinterpret_cast<const float2 *>(c->pinv);
+  const float2 *lntab = pinv_lntab(c, nb, ncheb);
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
     const size_t smem = (size_t)nb * 8;
     cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     ++c->launches;
-    k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, nullptr,
-                                                           nullptr, coef, mean, kg_out);
+    k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
+                                                           nullptr, nullptr, coef, mean, kg_out);
   } else {
     ++c->launches;
-    k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, c->sort_a,
-                                                        c->sort_b, coef, mean, kg_out);
+    k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
+                                                        c->sort_a, c->sort_b, coef, mean, kg_out);
   }
   return cudaGetLastError();
 }
@@ -681,14 +774,15 @@ cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double
 // ------------------------------------------------ allocation-free variant --
 // Scratch of helk_kdist_static in a file-scope device array instead of
 // cudaMalloc'd memory: the pseudo-inverse of the Chebyshev basis (N_b x
-// n_cheb doubles) followed by the Householder work array of the same size.
+// n_cheb doubles) followed by the Householder work array of the same size
+// and the logarithm's table.
 // Bins are limited to KDIST_STATIC_NB_MAX points (their sort then runs in
 // shared memory, so no other scratch is needed) and n_cheb to NCHEB_MAX:
 // 2 x 12288 x 32 x 8 B = 6 MiB, held by every device that loads the library
 // until the process exits.
 constexpr int64_t KDIST_STATIC_NB_MAX = 12288;
 constexpr int64_t KDIST_STATIC_PINV = KDIST_STATIC_NB_MAX * NCHEB_MAX;
-static __device__ __align__(256) double g_kdist_scratch[2 * KDIST_STATIC_PINV];
+static __device__ __align__(256) double g_kdist_scratch[2 * KDIST_STATIC_PINV + KD_LNTAB];
 
 namespace {
 constexpr int KDIST_STATIC_MAX_DEVICES = 64;
@@ -739,7 +833,8 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
     }
     ptr = S.ptr;
     if (S.nb != nb || S.ncheb != ncheb) {
-      k_pinv<<<1, PI_THREADS, 0, st>>>(nb, ncheb, ptr + KDIST_STATIC_PINV, nullptr, ptr);
+      k_pinv<<<1, PI_THREADS, 0, st>>>(nb, ncheb, ptr + KDIST_STATIC_PINV, nullptr, ptr,
+                                       reinterpret_cast<float2 *>(ptr + 2 * KDIST_STATIC_PINV));
       if (cudaGetLastError() != cudaSuccess) {
         S.nb = 0;
         S.ncheb = 0;
@@ -755,8 +850,9 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
     return HELK_ERR_CUDA;
   }
   k_kdist_bin<0><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor,
-                                                  reinterpret_cast<const float2 *>(ptr), nullptr, nullptr,
-                                                  coeffs, mean, kg_out);
+                                                  reinterpret_cast<const float2 *>(ptr),
+                                                  reinterpret_cast<const float2 *>(ptr + 2 * KDIST_STATIC_PINV),
+                                                  nullptr, nullptr, coeffs, mean, kg_out);
   return cudaGetLastError() == cudaSuccess ? HELK_OK : HELK_ERR_CUDA;
 }
 

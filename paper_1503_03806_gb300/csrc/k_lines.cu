@@ -393,7 +393,7 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // relative precision near the line centre.
 __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu,
                          const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
-                         int2 *__restrict__ core_all) {
+                         int2 *__restrict__ core_all, int32_t *__restrict__ ckey32) {
   const int cond = blockIdx.y;
   const LineRec64 *r64 = r64_all + (int64_t)cond * n;
   LineRec32 *r32 = r32_all + (int64_t)cond * n;
@@ -405,6 +405,8 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const LineRec64 r = r64[l];
+    const double key = ckey[l];
+    if (cond == 0) ckey32[l] = (int32_t)fmin(fmax(key, -2.0e9), 2.0e9);
     LineRec32 q;
     double cf = rint((r.nu0p - nu_min) / dnu);
     if (cf < -1.0e9) cf = -1.0e9;
@@ -442,8 +444,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
       const double dmax = ceil((10.001 + fabs((double)q.phi_k)) / (double)q.beta) + 1.0;
       const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
       if (clo <= chi) {
-        const double k = ckey[l];
-        const double w = fmax(k - clo, chi - k);
+        const double w = fmax(key - clo, chi - key);
         cw1 = max(cw1, (int)fmin(w + 1.0, 2.0e9));
         core = make_int2((int)clo, (int)chi);
       }
@@ -460,7 +461,7 @@ cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
   ++c->launches;
   k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->ckey, c->cstats, c->rec32,
-                                        c->core_rng);
+                                        c->core_rng, c->ckey32);
   return cudaGetLastError();
 }
 

@@ -498,30 +498,29 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 // the warp's own search), screened by each line's core range from the pack;
 // each thread adds S' K(|u|, a) of the lines whose core holds its point, in
 // list order (deterministic), or appends the point to the surrogate's queue
-// when routed.  Runs after k_voigt_f32 and
-// adds its sums (rescaled like the main kernel's) into kappa.  Few lines'
-// cores overlap at a point (~4 at the medium workload), so the plain FP32
-// sum loses < 1e-7 relative.
-constexpr int CORE_BLOCK = 256;
+// when routed.  The per-point sums go to kcore (every point written), so the
+// kernel can run beside k_voigt_f32; k_core_add then adds them into kappa,
+// rescaled like the main kernel's sums.  Few lines' cores overlap at a point
+// (~4 at the medium workload), so the plain FP32 sum loses < 1e-7 relative.
+constexpr int CORE_BLOCK = 128;
 
 template <bool COUNT>
 __global__ void __launch_bounds__(CORE_BLOCK)
     k_core_f32(const LineRec32 *__restrict__ rec_all, const int2 *__restrict__ core_all, int64_t nlines,
-               const double *__restrict__ ckey, int ngrid, double weight, double *__restrict__ kappa_all,
-               CondStats *cst, SurrQueue *sq) {
+               const int32_t *__restrict__ ckey, int ngrid, float *__restrict__ kcore_all, CondStats *cst,
+               SurrQueue *sq) {
   const int cond = blockIdx.y;
   const int cw1 = cst[cond].core_w1;
-  if (cw1 == 0) return;  // no line of the condition has a core
+  if (cw1 == 0) return;  // no line of the condition has a core (k_core_add skips it too)
   // each warp finds its own 32 points' candidate lines: no CTA barrier
   const int64_t A = (int64_t)blockIdx.x * CORE_BLOCK + (threadIdx.x & ~31);
   if (A >= ngrid) return;  // warp-uniform
   const int64_t B = min(A + 32, (int64_t)ngrid);
-  const double W = (double)(cw1 - 1);
-  const int64_t first = warp_search(ckey, 0, nlines, (double)A - W, false);
-  const int64_t last = warp_search(ckey, first, nlines, (double)(B - 1) + W, true);
+  const int64_t W = cw1 - 1;  // integer searches (FP64 is the scarce unit here)
+  const int64_t first = warp_search(ckey, 0, nlines, A - W, false);
+  const int64_t last = warp_search(ckey, first, nlines, B - 1 + W, true);
   const LineRec32 *rec = rec_all + (int64_t)cond * nlines;
   const int2 *core = core_all + (int64_t)cond * nlines;
-  const double scale = ldexp(weight, cst[cond].scale_exp);  // as k_voigt_f32's flush
   const int i = (int)(A + (threadIdx.x & 31));
   float v = 0.0f;
   unsigned long long n916 = 0, nterm = 0;
@@ -540,7 +539,7 @@ __global__ void __launch_bounds__(CORE_BLOCK)
         nterm += (unsigned long long)(n1 - n0 + 1);
       }
     }
-    if (v != 0.0f) kappa_all[(int64_t)cond * ngrid + i] += scale * (double)v;
+    kcore_all[(int64_t)cond * ngrid + i] = v;
   }
   if (COUNT) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -554,17 +553,41 @@ __global__ void __launch_bounds__(CORE_BLOCK)
   }
 }
 
-cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa) {
+// kappa += 2^E weight kcore at the points with a core sum (as k_voigt_f32's
+// flush scales its sums)
+__global__ void __launch_bounds__(256)
+    k_core_add(const float *__restrict__ kcore_all, int ngrid, double weight, double *__restrict__ kappa_all,
+               const CondStats *cst) {
+  const int cond = blockIdx.y;
+  if (cst[cond].core_w1 == 0) return;
+  const double scale = ldexp(weight, cst[cond].scale_exp);
+  const float *kcore = kcore_all + (int64_t)cond * ngrid;
+  double *kappa = kappa_all + (int64_t)cond * ngrid;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ngrid; i += gridDim.x * blockDim.x) {
+    const float v = kcore[i];
+    if (v != 0.0f) kappa[i] += scale * (double)v;
+  }
+}
+
+cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o) {
   if (o.precision != HELK_PREC_F32_KAHAN || c->nlines <= 0) return cudaSuccess;
   SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
   const dim3 grid((unsigned)((g.n + CORE_BLOCK - 1) / CORE_BLOCK), (unsigned)n_cond);
   ++c->launches;
   if (o.count_regions)
-    k_core_f32<true><<<grid, CORE_BLOCK, 0, c->stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey, (int)g.n,
-                                                          o.weight, kappa, c->cstats, sq);
+    k_core_f32<true><<<grid, CORE_BLOCK, 0, c->side_stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey32,
+                                                               (int)g.n, c->kcore, c->cstats, sq);
   else
-    k_core_f32<false><<<grid, CORE_BLOCK, 0, c->stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey, (int)g.n,
-                                                           o.weight, kappa, c->cstats, sq);
+    k_core_f32<false><<<grid, CORE_BLOCK, 0, c->side_stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey32,
+                                                                (int)g.n, c->kcore, c->cstats, sq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core_add(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa) {
+  if (o.precision != HELK_PREC_F32_KAHAN || c->nlines <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<int64_t>((g.n + 255) / 256, (int64_t)c->num_sms * 8), (unsigned)n_cond);
+  ++c->launches;
+  k_core_add<<<grid, 256, 0, c->stream>>>(c->kcore, (int)g.n, o.weight, kappa, c->cstats);
   return cudaGetLastError();
 }
 

@@ -31,14 +31,16 @@ static unsigned persistent_grid(helk_ctx *c, K kern, int block, int64_t nitems) 
 }
 
 // First index in [lo, hi) whose key is not below x (strict: key > x when
-// `upper`), else hi.  All lanes take part and get the result.
-__device__ __forceinline__ int64_t warp_search(const double *__restrict__ key, int64_t lo, int64_t hi, double x, bool upper) {
+// `upper`), else hi.  All lanes take part and get the result.  K: the key
+// type (double, or int32_t compared as integers against an int64_t x).
+template <typename K, typename X>
+__device__ __forceinline__ int64_t warp_search(const K *__restrict__ key, int64_t lo, int64_t hi, X x, bool upper) {
   const int lane = threadIdx.x & 31;
   // invariant: the answer lies in [lo, hi]
   while (hi - lo > 32) {
     const int64_t step = (hi - lo + 31) / 32;
     const int64_t p = lo + (int64_t)lane * step;
-    const bool below = p < hi && (upper ? key[p] <= x : key[p] < x);
+    const bool below = p < hi && (upper ? (X)key[p] <= x : (X)key[p] < x);
     const int c = __popc(__ballot_sync(0xffffffffu, below));
     const int64_t nlo = c > 0 ? lo + (int64_t)(c - 1) * step + 1 : lo;
     const int64_t nhi = c > 0 ? min(hi, lo + (int64_t)c * step) : lo;
@@ -46,7 +48,7 @@ __device__ __forceinline__ int64_t warp_search(const double *__restrict__ key, i
     hi = nhi;
   }
   const int64_t p = lo + lane;
-  const bool below = p < hi && (upper ? key[p] <= x : key[p] < x);
+  const bool below = p < hi && (upper ? (X)key[p] <= x : (X)key[p] < x);
   return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 

@@ -64,12 +64,15 @@ static __device__ __noinline__ double k916_f64(double x, double y, double erfcx_
 // FP32 resolution.  The recurrences start at the low end of the summed range
 // (terms ~e^{-18.5}), so nothing overflows or underflows.
 constexpr float A916_TAIL_F32 = 4.3f;
-constexpr int A916_TERMS_F32 = 20;  // n1 - n0 + 1 <= 2 (2 * 4.3 + 1) + 1 = 20.2
+// n in [2(x - 4.3), 2(x + 4.3)], an interval of length 17.2: at most 18 terms
+constexpr int A916_TERMS_F32 = 18;
+// S2 terms e^{-(nh+x)^2} within the window have nh < 4.3: n <= 8
+constexpr int A916_S2_TERMS_F32 = 8;
 
 static __device__ __forceinline__ void a916_range_f32(float x, int &n0, int &n1) {
-  n0 = (int)floorf((x - A916_TAIL_F32) * 2.0f);
+  n0 = (int)ceilf((x - A916_TAIL_F32) * 2.0f);
   if (n0 < 1) n0 = 1;
-  n1 = (int)ceilf((x + A916_TAIL_F32) * 2.0f);
+  n1 = (int)floorf((x + A916_TAIL_F32) * 2.0f);
 }
 
 static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
@@ -95,9 +98,11 @@ static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y
   // Beyond x = A916_TAIL_F32 - h every S2 term e^{-(nh+x)^2}, n >= 1, is
   // below e^{-18.49} (outside the window): when that holds for all the
   // warp's active lanes, the S2 recurrence is left out (a warp-uniform
-  // choice, so the lanes stay in lockstep).
+  // choice, so the lanes stay in lockstep).  Otherwise it runs over the
+  // first A916_S2_TERMS_F32 terms only (for a lane with n0 > 1 those are
+  // far outside the window and add nothing).
   if (__all_sync(__activemask(), x > A916_TAIL_F32 - h)) {
-#pragma unroll 4
+#pragma unroll 6
     for (int t = 0; t < A916_TERMS_F32; ++t) {
       s23 += __fdividef(E3, fmaf(nhn, nhn, y2));
       E3 *= R3;
@@ -108,12 +113,19 @@ static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y
     float E2 = expf(-(dp * dp));
     float R2 = expf(-(2.0f * h * dp + h * h));
 #pragma unroll 4
-    for (int t = 0; t < A916_TERMS_F32; ++t) {
+    for (int t = 0; t < A916_S2_TERMS_F32; ++t) {
       s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
       E3 *= R3;
       R3 *= q;
       E2 *= R2;
       R2 *= q;
+      nhn += h;
+    }
+#pragma unroll 5
+    for (int t = A916_S2_TERMS_F32; t < A916_TERMS_F32; ++t) {
+      s23 += __fdividef(E3, fmaf(nhn, nhn, y2));
+      E3 *= R3;
+      R3 *= q;
       nhn += h;
     }
   }
