@@ -231,6 +231,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_smem, uint32_t p
   return false;
 }
 
+// The lanes of the warp whose 8-bit digit equals this lane's (what a
+// match-any over the digit gives), from eight ballots, one per digit bit: a
+// fixed cost, where a match-any's cost grows with the number of distinct
+// values among the lanes.  Lanes with valid == false match no lane; their
+// own result is their own bit.
+__device__ __forceinline__ uint32_t warp_digit_peers(uint32_t d, bool valid) {
+  uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? m : ~m;
+  }
+  return valid ? peers : (1u << (threadIdx.x & 31));
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

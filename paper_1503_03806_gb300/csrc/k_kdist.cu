@@ -308,9 +308,10 @@ __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned lo
     __syncthreads();
     for (int e0 = w0; e0 < w1; e0 += 32) {
       const int e = e0 + lane;
-      const uint32_t d = e < w1 ? (uint32_t)((A[e] >> shift) & 0xFF) : 256u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (d < 256 && (peers & lanemask_lt_kd()) == 0) hist[hidx(d, w)] += __popc(peers);
+      const bool valid = e < w1;
+      const uint32_t d = valid ? (uint32_t)((A[e] >> shift) & 0xFF) : 0u;
+      const uint32_t peers = warp_digit_peers(d, valid);
+      if (valid && (peers & lanemask_lt_kd()) == 0) hist[hidx(d, w)] += __popc(peers);
     }
     __syncthreads();
     block_exscan_4096(hist, wtot);
@@ -318,8 +319,8 @@ __device__ unsigned long long *cta_radix_sort(unsigned long long *A, unsigned lo
       const int e = e0 + lane;
       const bool valid = e < w1;
       const unsigned long long k = valid ? A[e] : 0ull;
-      const uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 0u;
+      const uint32_t peers = warp_digit_peers(d, valid);
       if (valid) B[hist[hidx(d, w)] + __popc(peers & lanemask_lt_kd())] = k;
       __syncwarp();
       if (valid && (peers & lanemask_lt_kd()) == 0) hist[hidx(d, w)] += __popc(peers);
@@ -360,8 +361,8 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
         const int e = w0 + 32 * i + lane;
         const bool valid = e < w1;
         key[i] = valid ? A[e] : 0ull;
-        const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFFull) : 256u + lane;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFFull) : 0u;
+        const uint32_t peers = warp_digit_peers(d, valid);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (valid && lane == leader) {

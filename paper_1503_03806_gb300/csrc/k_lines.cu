@@ -69,7 +69,7 @@ cudaError_t launch_validate_lines(helk_ctx *c, int64_t n) {
 // Keys: 64-bit, values: 32-bit.  One pass per 8-bit digit; each pass is
 // upsweep (per-tile digit counts) -> exclusive scan -> downsweep (stable
 // scatter: warps own consecutive sub-ranges, ranks inside a warp batch come
-// from __match_any_sync).
+// from the digit's peer lanes).
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_TILE = 4096;  // elements per block
@@ -142,9 +142,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
   // per-warp digit counts
   for (int64_t e0 = w0; e0 < w1; e0 += 32) {
     int64_t e = e0 + lane;
-    uint32_t d = e < w1 ? (uint32_t)((kin[e] >> shift) & 0xFF) : 256u + lane;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d < 256 && (peers & lanemask_lt()) == 0) h[d * RS_WARPS + w] += __popc(peers);
+    const bool valid = e < w1;
+    uint32_t d = valid ? (uint32_t)((kin[e] >> shift) & 0xFF) : 0u;
+    uint32_t peers = warp_digit_peers(d, valid);
+    if (valid && (peers & lanemask_lt()) == 0) h[d * RS_WARPS + w] += __popc(peers);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
     int64_t e = e0 + lane;
     bool valid = e < w1;
     unsigned long long k = valid ? kin[e] : 0ull;
-    uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u + lane;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 0u;
+    uint32_t peers = warp_digit_peers(d, valid);
     if (valid) {
       uint32_t pos = h[d * RS_WARPS + w] + __popc(peers & lanemask_lt());
       kout[pos] = k;
