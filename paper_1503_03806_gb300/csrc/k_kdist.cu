@@ -352,9 +352,12 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
     const int shift = pass * 8;
     if (((diff >> shift) & 0xFFull) == 0) continue;
     for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
-    __syncthreads();
     unsigned long long key[KD_ITEMS];
-    uint32_t code[KD_ITEMS];  // digit | (rank among earlier keys of the digit) << 8
+    // Per key: digit | rank among the item's earlier lanes of the digit << 8
+    // | the digit group's lowest lane << 13 | (group size, on that lane) << 18.
+    // The items are independent here (no shared-memory writes), so their
+    // loads and ballots overlap.
+    uint32_t code[KD_ITEMS];
 #pragma unroll
     for (int i = 0; i < KD_ITEMS; ++i) {
       if (w0 + 32 * i < w1) {  // warp-uniform
@@ -363,14 +366,25 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
         key[i] = valid ? A[e] : 0ull;
         const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFFull) : 0u;
         const uint32_t peers = warp_digit_peers(d, valid);
-        const int leader = __ffs(peers) - 1;
+        const uint32_t below = peers & lt;
+        const uint32_t cnt = (valid && below == 0) ? (uint32_t)__popc(peers) : 0u;
+        code[i] = d | ((uint32_t)__popc(below) << 8) | ((uint32_t)(__ffs(peers) - 1) << 13) | (cnt << 18);
+      }
+    }
+    __syncthreads();  // counters zeroed
+    // Running per-(digit, warp) counts, item by item: the only serial chain
+    // is the group leaders' read-add-write of their counters.
+#pragma unroll
+    for (int i = 0; i < KD_ITEMS; ++i) {
+      if (w0 + 32 * i < w1) {
+        const uint32_t cd = code[i], d = cd & 0xFFu, cnt = cd >> 18;
         uint32_t old = 0;
-        if (valid && lane == leader) {
+        if (cnt) {
           old = hist[hidx(d, w)];
-          hist[hidx(d, w)] = old + __popc(peers);
+          hist[hidx(d, w)] = old + cnt;
         }
-        old = __shfl_sync(0xffffffffu, old, leader);
-        code[i] = (d & 0xFFu) | ((old + __popc(peers & lt)) << 8);
+        old = __shfl_sync(0xffffffffu, old, (int)((cd >> 13) & 31u));
+        code[i] = d | ((old + ((cd >> 8) & 31u)) << 8);
         __syncwarp();
       }
     }
@@ -383,6 +397,63 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
     }
     __syncthreads();
   }
+}
+
+// Bucket sort of a bin held in shared memory: the keys' range [kmin, kmax]
+// is cut into KD_NBUCKET buckets of equal width in key space (the key bits
+// are monotone in the value and close to its logarithm), the keys are
+// counted and scattered into B by bucket (shared-memory atomics, any order
+// within a bucket), and each key's place is its bucket's start plus the
+// number of keys of the bucket that are smaller, or equal and earlier in B.
+// Equal keys are equal values, so the result does not depend on the scatter
+// order.  The ranking is quadratic in the bucket size: when a bucket holds
+// more than KD_BUCKET_MAX keys this returns false with A untouched, and the
+// caller radix-sorts instead.
+constexpr int KD_NBUCKET = KD_THREADS * 8;  // block_exscan_4096's counters
+constexpr int KD_BUCKET_MAX = 512;
+
+__device__ __forceinline__ int hpad(int b) { return b + (b >> 4); }  // block_exscan_4096's layout
+
+__device__ bool cta_bucket_sort(unsigned long long *A, unsigned long long *B, int nb, uint32_t *hist,
+                                uint32_t *wtot, unsigned long long kmin, unsigned long long kmax) {
+  const int tid = threadIdx.x;
+  const int sh = max(0, 64 - __clzll((long long)(kmax - kmin)) - 12);  // (kmax - kmin) >> sh < 4096
+  for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
+  __syncthreads();
+  // neighbouring grid points have close values: the lanes of a warp take keys
+  // 97 apart, so that their atomics mostly go to different counters
+  const int pt = (tid * 97) & (KD_THREADS - 1);
+  for (int j0 = 0; j0 < nb; j0 += KD_THREADS) {
+    const int j = j0 + pt;
+    if (j < nb) atomicAdd(&hist[hpad((int)((A[j] - kmin) >> sh))], 1u);
+  }
+  __syncthreads();
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m = max(m, hist[hpad(tid * 8 + i)]);
+  if (__syncthreads_or(m > (uint32_t)KD_BUCKET_MAX)) return false;
+  block_exscan_4096(hist, wtot);  // bucket starts
+  for (int j0 = 0; j0 < nb; j0 += KD_THREADS) {
+    const int j = j0 + pt;
+    if (j < nb) {
+      const unsigned long long k = A[j];
+      B[atomicAdd(&hist[hpad((int)((k - kmin) >> sh))], 1u)] = k;
+    }
+  }
+  __syncthreads();  // hist now holds each bucket's end
+  for (int j = tid; j < nb; j += KD_THREADS) {
+    const unsigned long long k = B[j];
+    const int b = (int)((k - kmin) >> sh);
+    const int lo = b > 0 ? (int)hist[hpad(b - 1)] : 0, hi = (int)hist[hpad(b)];
+    int r = lo;
+    for (int i = lo; i < hi; ++i) {
+      const unsigned long long x = B[i];
+      r += (x < k) || (x == k && i < j);
+    }
+    A[r] = k;
+  }
+  __syncthreads();
+  return true;
 }
 
 // Sort by the high 32 bits (sign, exponent, top 20 fraction bits) first: 4
@@ -528,8 +599,9 @@ __device__ __forceinline__ float2 ff_warp_sum8(const float2 (&v)[8], int lane) {
   return ff_add(r, shfl_xor_f2(r, 1));
 }
 
-// Per-bin sort + fit.  MODE 0: keys in shared memory (nb <= KD_REG_MAX,
-// register-resident passes, one array); MODE 1: keys in the global ping-pong
+// Per-bin sort + fit.  MODE 0: keys in shared memory (nb <= KD_REG_MAX, two
+// arrays: bucket sort, else register-resident radix passes); MODE 1: keys in
+// the global ping-pong
 // buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
 template <int MODE>
 __global__ void __launch_bounds__(KD_THREADS)
@@ -540,19 +612,21 @@ __global__ void __launch_bounds__(KD_THREADS)
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t hist[KD_HIST];
   __shared__ uint32_t wtot[32];
-  __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS];
+  __shared__ unsigned long long red_and[KD_WARPS], red_or[KD_WARPS], red_min[KD_WARPS], red_max[KD_WARPS];
   __shared__ float2 red[KD_WARPS][NCHEB_MAX];
   __shared__ unsigned long long red_fx[KD_WARPS][2];
   __shared__ float2 s_lnc[128], s_invc[128];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t off = (int64_t)blockIdx.x * nb;
   unsigned long long *A = MODE == 0 ? (unsigned long long *)dsm : gA + off;
-  unsigned long long vand = ~0ull, vor = 0ull;
+  unsigned long long vand = ~0ull, vor = 0ull, vmin = ~0ull, vmax = 0ull;
   for (int j = tid; j < nb; j += KD_THREADS) {
     const unsigned long long k = (unsigned long long)__double_as_longlong(kappa[off + j]);
     A[j] = k;
     vand &= k;
     vor |= k;
+    vmin = min(vmin, k);
+    vmax = max(vmax, k);
   }
   if (tid < KD_LNTAB) {  // ln c_j and 1/c_j as FP32 (high, low) pairs
     const float2 t = lntab[tid];
@@ -564,21 +638,31 @@ __global__ void __launch_bounds__(KD_THREADS)
   for (int o = 16; o > 0; o >>= 1) {
     vand &= __shfl_down_sync(0xffffffffu, vand, o);
     vor |= __shfl_down_sync(0xffffffffu, vor, o);
+    vmin = min(vmin, __shfl_down_sync(0xffffffffu, vmin, o));
+    vmax = max(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
   }
   if (lane == 0) {
     red_and[w] = vand;
     red_or[w] = vor;
+    red_min[w] = vmin;
+    red_max[w] = vmax;
   }
   __syncthreads();
   vand = ~0ull;
   vor = 0ull;
+  vmin = ~0ull;
+  vmax = 0ull;
   for (int i = 0; i < KD_WARPS; ++i) {
     vand &= red_and[i];
     vor |= red_or[i];
+    vmin = min(vmin, red_min[i]);
+    vmax = max(vmax, red_max[i]);
   }
   unsigned long long *S;
   if (MODE == 0) {
-    cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
+    // the second key array of the bucket sort follows A in shared memory
+    if (vmin != vmax && !cta_bucket_sort(A, A + nb, nb, hist, wtot, vmin, vmax))
+      cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
     S = A;
   } else {
     S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
@@ -665,10 +749,10 @@ __global__ void __launch_bounds__(KD_THREADS)
 }
 
 int64_t kdist_smem_max_points(helk_ctx *c) {
-  // one shared-memory key array (8 B a point) beside ~26 KB of static smem
+  // two shared-memory key arrays (16 B a point) beside ~26 KB of static smem
   const int64_t fixed = 26 * 1024;
   const int64_t avail = (int64_t)c->max_smem_optin - fixed;
-  return std::min<int64_t>(KD_REG_MAX, avail > 0 ? avail / 8 : 0);
+  return std::min<int64_t>(KD_REG_MAX, avail > 0 ? avail / 16 : 0);
 }
 
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
@@ -677,7 +761,7 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   const float2 *P = reinterpret_cast<const float2 *>(c->pinv);
   const float2 *lntab = pinv_lntab(c, nb, ncheb);
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
-    const size_t smem = (size_t)nb * 8;
+    const size_t smem = (size_t)nb * 16;
     cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -816,7 +900,7 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
   int smem_optin = 0;
   if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return HELK_ERR_CUDA;
-  const size_t smem = (size_t)nb * 8;
+  const size_t smem = (size_t)nb * 16;
   if ((int64_t)smem + 26 * 1024 > smem_optin) return HELK_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double *ptr;

@@ -1,7 +1,8 @@
 """GPU parity of the k-distribution stage (Sec. 2.2, 2.6).
 
 Sorted values: bit-exact against the oracle's library sort on identical
-input.  Chebyshev coefficients: the GPU applies the pseudo-inverse of the
+input, on both sort paths of a shared-memory bin (bucket sort; radix passes
+when a bucket is crowded, e.g. by many equal values).  Chebyshev coefficients: the GPU applies the pseudo-inverse of the
 design matrix shared by all bins (one Householder QR per bin size), the
 oracle runs a Householder QR per bin; both are backward stable and the basis
 is well conditioned at the workloads' bin sizes (cond(A) ~ 5), so the
@@ -86,17 +87,32 @@ def _tied_high_words(n, group, seed):
     return bits.view(np.float64)
 
 
+def _with_zeros(k, nbins, nzero):
+    """The same opacities with the first nzero points of every bin set to 0:
+    more than 512 equal keys fill one bucket of the bucket sort, so the bin
+    takes the radix-sort path instead."""
+    k = k.copy().reshape(nbins, -1)
+    k[:, :nzero] = 0.0
+    return k.reshape(-1)
+
+
 def test_high_word_ties_short_runs(ctx):
-    # runs of 2..5 keys equal in the high word: sorted by the low word after
-    # the high-word passes
+    # runs of 2..5 keys equal in the high word: in one bucket of the bucket
+    # sort; on the radix path (zeros added) sorted by the low word after the
+    # high-word passes
     for group in (2, 3, 5):
-        check_kdist(ctx, _tied_high_words(4 * 9000, group, 20 + group), 4, 20)
+        k = _tied_high_words(4 * 9000, group, 20 + group)
+        check_kdist(ctx, k, 4, 20)
+        check_kdist(ctx, _with_zeros(k, 4, 600), 4, 20, floor=1e-40)
 
 
 def test_high_word_ties_long_runs(ctx):
-    # runs longer than one thread sorts (and a long run of zeros beside an
-    # unsorted short one): the bin is sorted again by all eight bytes
-    check_kdist(ctx, _tied_high_words(3 * 8000, 200, 31), 3, 20)
+    # runs longer than one thread sorts on the radix path: the bin is sorted
+    # again by all eight bytes (also a long run of zeros beside an unsorted
+    # short one); runs of 200 in one bucket of the bucket sort
+    k = _tied_high_words(3 * 8000, 200, 31)
+    check_kdist(ctx, k, 3, 20)
+    check_kdist(ctx, _with_zeros(k, 3, 600), 3, 20, floor=1e-40)
     k = _tied_high_words(2 * 6000, 2, 32)
     k[:2000] = 0.0
     check_kdist(ctx, k, 2, 20, floor=1e-40)
