@@ -139,6 +139,7 @@ void helk_destroy(helk_ctx *c) {
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->side_stream) cudaStreamSynchronize(c->side_stream);
   if (c->mass_col) cudaFree(c->mass_col);
   for (void *p : {(void *)c->mlp_p, (void *)c->mlp_m, (void *)c->mlp_v, (void *)c->mlp_g,
                   (void *)c->mlp_loss, (void *)c->mlp_feat, (void *)c->mlp_tgt, (void *)c->mlp_mask,

@@ -271,6 +271,7 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
   long long wmax = -1;
   unsigned long long spmax = 0;
   const double vth = sqrt(2.0 * LN2 * KB * C.T / (A.mass * AMU)) / CLIGHT;
+  const double tfac_half = sqrt(T0 / C.T);  // (T0/T)^n for the usual n = 1/2
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = nu0[l];
@@ -287,13 +288,25 @@ __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const doub
       S = S * C.q_ratio * boltz * stim;
     }
     if (lweight) S = S * lweight[l];
-    const double tfac = (nc == 0.5) ? sqrt(T0 / C.T) : pow(T0 / C.T, nc);
+    const double tfac = (nc == 0.5) ? tfac_half : pow(T0 / C.T, nc);
     const double pself = 0.5 * C.P;
     const double gL = tfac * (ga * (C.P - pself) + gs * pself);
     const double gD = nu0p * (lmass ? sqrt(2.0 * LN2 * KB * C.T / (lmass[l] * AMU)) / CLIGHT : vth);
-    const double a = SQRTLN2 * gL / gD;
-    const double ku = SQRTLN2 / gD;
-    const double Sp = S * SQRTLN2PI / gD;
+    // The FP64 form divides (a and k_u are then the correctly rounded results
+    // the oracle computes, so every method choice matches it); the FP32 form
+    // rounds them to FP32 anyway and multiplies by one reciprocal (FP64
+    // divisions are long sequences on the scarce FP64 unit).
+    double a, ku, Sp;
+    if (a916_f64) {
+      a = SQRTLN2 * gL / gD;
+      ku = SQRTLN2 / gD;
+      Sp = S * SQRTLN2PI / gD;
+    } else {
+      const double igD = 1.0 / gD;
+      a = SQRTLN2 * gL * igD;
+      ku = SQRTLN2 * igD;
+      Sp = S * SQRTLN2PI * igD;
+    }
     double cut;
     if (A.cut_kind == HELK_CUT_ABS) cut = A.cut_value;
     else if (A.cut_kind == HELK_CUT_LORENTZ) cut = fmin(A.cut_value * gL, A.cut_cap);
@@ -402,6 +415,8 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
   const double spmax = __longlong_as_double((long long)cst->spmax_bits);
   const int E = spmax > 0.0 ? ilogb(spmax) + 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) cst->scale_exp = E;
+  const double pow2mE = ldexp(1.0, -E);  // exact: S' 2^-E by one multiplication
+  const double idnu = 1.0 / dnu;
   int cw1 = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
@@ -409,7 +424,9 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     const double key = ckey[l];
     if (cond == 0) ckey32[l] = (int32_t)fmin(fmax(key, -2.0e9), 2.0e9);
     LineRec32 q;
-    double cf = rint((r.nu0p - nu_min) / dnu);
+    // any integer within a step of the centre serves as c (phi takes the
+    // rest), so a product by 1/dnu replaces the division
+    double cf = rint((r.nu0p - nu_min) * idnu);
     if (cf < -1.0e9) cf = -1.0e9;
     if (cf > 1.0e9) cf = 1.0e9;
     q.c = (int32_t)cf;
@@ -419,7 +436,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     q.beta = (float)(dnu * r.ku);
     q.a = (float)r.a;
     q.a2 = (float)r.a2;
-    const double sp = ldexp(r.Sp, -E);
+    const double sp = r.Sp * pow2mE;
     q.P1 = (float)(sp * r.a * INV_SQRTPI);
     q.P3 = (float)(sp * r.a * (SQRTPI / 6.0) / PI);
     q.Sp = (float)sp;
@@ -442,7 +459,8 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     // reference index bounds the core kernel's candidate search.
     int2 core = make_int2(1, 0);
     if (q.a2 < 100.0f && q.ihi >= q.ilo && q.beta > 0.0f) {
-      const double dmax = ceil((10.001 + fabs((double)q.phi_k)) / (double)q.beta) + 1.0;
+      // an upper bound (FP32 quotient, rounding covered by the margin of 2)
+      const double dmax = (double)ceilf((10.001f + fabsf(q.phi_k)) / q.beta) + 2.0;
       const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
       if (clo <= chi) {
         const double w = fmax(key - clo, chi - key);
