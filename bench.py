@@ -320,7 +320,7 @@ def run_ours(args):
                 "peak_basis": "%s pipe: %d FMA/clk/SM x %d SMs x %.0f MHz max clock (derived)"
                               % (form.upper(), FMA_PER_CLK_SM[form], nsm, max_mhz),
                 "flops_per_launch": flops, "voigt_ms_per_launch": voigt_s * 1e3,
-                "tile_points": tile}
+                "kernel_shape": helk.helk_tile_shape(prec, tile)}
         return {"form": form, "evals": evals, "reg": [int(x) for x in reg], "ms_step": ms_step,
                 "launches": launches,
                 "value": world * evals / (ms_step * 1e-3), "roofline": roof, "wall": wall,
@@ -407,7 +407,7 @@ def run_ours(args):
                "form": "FP32 + Kahan, one graph-captured persistent launch per call",
                "ms_per_call": ms_b, "ms_per_condition": ms_b / len(Ts),
                "evals_per_call": int(ev_b.sum()), "value": int(ev_b.sum()) / (ms_b * 1e-3),
-               "unit": UNIT, "tile_points": tile_b,
+               "unit": UNIT, "kernel_shape": helk.helk_tile_shape(PREC["f32"], tile_b),
                "stages_ms_per_call": {k: v[0] / max(1, v[1]) for k, v in st_b.items() if v[1]}}
         del kb
         ctx.upload(lines)
@@ -553,8 +553,8 @@ def run_profile_case(form):
     ctx.upload(synth.workload_lines(WORKLOAD))
     grid = (w["nu_min"], w["dnu"], w["ngrid"])
     tile = ctx.autotune(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], grid, precision=prec)
-    print("profile case %s: %d autotune launches of the Voigt kernel, then tile %d"
-          % (form, 4 * len(helk.helk_tile_candidates(prec)), tile), flush=True)
+    print("profile case %s: %d autotune launches of the Voigt kernel, then shape %s"
+          % (form, 4 * len(helk.helk_tile_candidates(prec)), helk.helk_tile_shape(prec, tile)), flush=True)
     kappa = torch.empty(w["ngrid"], dtype=torch.float64, device="cuda")
     for _ in range(2):
         ctx.opacity(w["T"][0], w["P_atm"][0], w["mass"], w["cut"], (w["nu_min"], w["dnu"], w["ngrid"]),

@@ -213,26 +213,36 @@ helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
                        double *coeffs, double *mean, int32_t out_on_host,
                        double *kg_out);
 
-/* Autotuner of the Voigt kernel's tile shape.  Runs the line preparation of
- * this condition once, then times every built tile shape (points per CTA)
- * of opts->precision on it (three launches each, CUDA events on the context
- * stream) and keeps the fastest for later helk_opacity calls with the same
- * precision and grid size; other sizes fall back to the built-in choice
- * (tiles filling whole waves of resident CTAs).  *tile_out (optional)
- * receives the chosen points per tile.  Overwrites the context's own
+/* Autotuner of the Voigt kernel's shape.  A shape is one built
+ * configuration of a precision's persistent Voigt kernel: the tile (grid
+ * points per CTA tile), the warps per CTA and the candidate lines per
+ * pipeline stage; it is named by a shape code (helk_tile_shape decodes it).
+ * Runs the line preparation of this condition once, then times every
+ * candidate shape of opts->precision on it (three launches each, CUDA events
+ * on the context stream) and keeps the fastest for later helk_opacity calls
+ * with the same precision and grid size; other sizes fall back to the
+ * built-in choice (tiles filling whole waves of resident CTAs).  *tile_out
+ * (optional) receives the chosen shape code.  Overwrites the context's own
  * opacity buffer; synchronises. */
 helk_status helk_autotune(helk_ctx *ctx, double T, double P_atm,
                           double mass_amu, const helk_cutoff *cut,
                           const helk_grid *grid, const helk_opts *opts,
                           int32_t *tile_out);
 
-/* The built Voigt tile shapes of a precision (points per CTA tile,
- * ascending): writes up to `max` of them to out (host memory) and returns
- * how many there are.  No device work; returns 0 for an unknown precision
- * or out == NULL. */
+/* The shape codes of a precision that the autotuner times (FP32: the
+ * 1-based positions of its built shapes; FP64: slots per warp, 4, 6, 8):
+ * writes up to `max` of them to out (host memory) and returns how many there
+ * are.  No device work; returns 0 for an unknown precision or out == NULL. */
 int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max);
 
-/* Fixes the Voigt tile shape of `precision` for grids of n points (what
+/* Decodes a shape code of `precision`: points per CTA tile, warps per CTA
+ * and candidate lines per pipeline stage (each output optional, host
+ * memory).  HELK_ERR_INVALID_ARG for an unknown precision or code.  No
+ * device work. */
+helk_status helk_tile_shape(int32_t precision, int32_t code, int32_t *points,
+                            int32_t *warps, int32_t *lines_per_stage);
+
+/* Fixes the Voigt kernel shape of `precision` for grids of n points (what
  * helk_autotune would store), or, with tile == 0, returns to the built-in
  * choice.  tile must be one of helk_tile_candidates(precision); anything
  * else returns HELK_ERR_INVALID_ARG.  The shape changes no FP64 result and

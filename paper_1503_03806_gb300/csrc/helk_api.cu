@@ -387,8 +387,15 @@ static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single
 }
 
 // Tile map, condition order and the persistent Voigt kernel.
+// Points per CTA tile of a shape code returned by voigt_shape or the candidates.
+static int shape_points(int precision, int shape) {
+  int p = 0;
+  return voigt_shape_info(precision, shape, &p, nullptr, nullptr) ? p : 1;
+}
+
+// `shape`: the Voigt kernel's shape code; `tile`: its points per CTA tile.
 static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const helk_opts &o, double *kappa,
-                             int tile, int64_t ntiles) {
+                             int shape, int tile, int64_t ntiles) {
   HELK_TRY(cuda_check(c, launch_tilemap(c, n_cond, *g, tile, ntiles), "tilemap"));
   HELK_TRY(cuda_check(c, launch_cond_order(c, n_cond), "condition order"));
   HELK_TRY(cuda_check(c, cudaMemsetAsync(&c->stats->tile_counter, 0, sizeof(unsigned int), c->stream),
@@ -400,14 +407,14 @@ static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const 
     // (whose CTAs are issued first and leave registers and warp slots on every
     // SM), into their own buffer; their sums are added once both are done.
     HELK_TRY(cuda_check(c, cudaEventRecord(c->fork_ev, c->stream), "voigt"));
-    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, shape, ntiles), "voigt"));
     HELK_TRY(cuda_check(c, cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0), "voigt cores"));
     HELK_TRY(cuda_check(c, launch_voigt_core(c, n_cond, *g, o), "voigt cores"));
     HELK_TRY(cuda_check(c, cudaEventRecord(c->join_ev, c->side_stream), "voigt cores"));
     HELK_TRY(cuda_check(c, cudaStreamWaitEvent(c->stream, c->join_ev, 0), "voigt cores"));
     HELK_TRY(cuda_check(c, launch_core_add(c, n_cond, *g, o, kappa), "voigt cores"));
   } else {
-    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, tile, ntiles), "voigt"));
+    HELK_TRY(cuda_check(c, launch_voigt(c, n_cond, *g, o, kappa, shape, ntiles), "voigt"));
   }
   if (o.surrogate) HELK_TRY(cuda_check(c, launch_mlp_queue(c, n_cond, g->n, o.weight, kappa), "surrogate"));
   return HELK_OK;
@@ -426,7 +433,8 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
     HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
     kappa = c->kappa;
   }
-  const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
+  const int shape = voigt_shape(c, o.precision, o.count_regions, g->n);
+  const int tile = shape_points(o.precision, shape);
   const int64_t ntiles = (g->n + tile - 1) / tile;
   HELK_TRY(ensure_call_buffers(c, 1, o, ntiles, g->n));
   const CondArgs one{T, P, o.q_ratio, 0.0};
@@ -435,7 +443,7 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   stage_end(c, HELK_STAGE_LINEPREP);
   if (c->nlines > 0) {
     stage_begin(c, HELK_STAGE_VOIGT);
-    HELK_TRY(run_voigt(c, 1, g, o, kappa, tile, ntiles));
+    HELK_TRY(run_voigt(c, 1, g, o, kappa, shape, tile, ntiles));
     stage_end(c, HELK_STAGE_VOIGT);
   } else if (!o.accumulate) {
     HELK_TRY(cuda_check(c, cudaMemsetAsync(kappa, 0, (size_t)g->n * 8, c->stream), "opacity"));
@@ -460,10 +468,13 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   HELK_TRY(ensure_buf(c, (void **)&c->kappa, &c->kappa_cap, g->n * 8, "opacity buffer"));
   const int prec = o.precision == HELK_PREC_F32_KAHAN ? 1 : 0;
   c->tuned_tile[prec] = 0;  // time the candidates, not the previous choice
-  int cand[16];
-  const int ncand = voigt_tile_candidates(o.precision, cand, 16);
+  int cand[32];
+  const int ncand = voigt_shape_candidates(o.precision, cand, 32);
   int64_t max_tiles = 0;
-  for (int i = 0; i < ncand; ++i) max_tiles = std::max(max_tiles, (g->n + cand[i] - 1) / cand[i]);
+  for (int i = 0; i < ncand; ++i) {
+    const int pts = shape_points(o.precision, cand[i]);
+    max_tiles = std::max(max_tiles, (g->n + pts - 1) / pts);
+  }
   HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles, g->n));
   const CondArgs one{T, P, o.q_ratio, 0.0};
   HELK_TRY(prepare_lines(c, 1, &one, mass, cut, g, o));
@@ -477,12 +488,13 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   int best = cand[0];
   helk_status st = HELK_OK;
   for (int i = 0; i < ncand && st == HELK_OK; ++i) {
-    const int64_t ntiles = (g->n + cand[i] - 1) / cand[i];
-    st = run_voigt(c, 1, g, o, c->kappa, cand[i], ntiles);  // warm-up
+    const int pts = shape_points(o.precision, cand[i]);
+    const int64_t ntiles = (g->n + pts - 1) / pts;
+    st = run_voigt(c, 1, g, o, c->kappa, cand[i], pts, ntiles);  // warm-up
     float ms = 0.f;
     const int reps = 3;
     if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e0, c->stream), "autotune");
-    for (int r = 0; r < reps && st == HELK_OK; ++r) st = run_voigt(c, 1, g, o, c->kappa, cand[i], ntiles);
+    for (int r = 0; r < reps && st == HELK_OK; ++r) st = run_voigt(c, 1, g, o, c->kappa, cand[i], pts, ntiles);
     if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e1, c->stream), "autotune");
     if (st == HELK_OK) st = cuda_check(c, cudaEventSynchronize(e1), "autotune");
     if (st == HELK_OK) st = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "autotune");
@@ -508,12 +520,12 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
 // FP32 records, tile maps, condition order, Voigt kernel) is captured once
 // into a CUDA graph per call shape and replayed.
 static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const helk_cutoff *cut,
-                             const helk_grid *g, const helk_opts &o, const double *kappa, int tile) {
+                             const helk_grid *g, const helk_opts &o, const double *kappa, int shape) {
   char b[512];
   snprintf(b, sizeof b, "%d|%lld|%p|%a|%d|%a|%a|%a|%a|%lld|%d|%d|%a|%d|%d|%p|%d|%p|%p|%p|%p|%p|%p", n_cond,
            (long long)c->nlines, (const void *)c->nu0, mass, cut->kind, cut->value, cut->cap, g->nu_min,
            g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions, o.surrogate,
-           (const void *)kappa, tile, (const void *)c->rec64, (const void *)c->rec32,
+           (const void *)kappa, shape, (const void *)c->rec64, (const void *)c->rec32,
            (const void *)c->tile_lo, (const void *)c->cstats, (const void *)c->squeue, (const void *)c->kcore);
   return std::string(b);
 }
@@ -547,7 +559,8 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
     c->have_opacity = (kappa == c->kappa);
     return HELK_OK;
   }
-  const int tile = voigt_tile_len(c, o.precision, o.count_regions, g->n);
+  const int shape = voigt_shape(c, o.precision, o.count_regions, g->n);
+  const int tile = shape_points(o.precision, shape);
   const int64_t ntiles = (g->n + tile - 1) / tile;
   HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles, g->n));
   if (!c->cap_stream)
@@ -556,7 +569,7 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
   // the previous batch must have read the staging buffer before it changes
   HELK_TRY(cuda_check(c, cudaEventSynchronize(c->cond_ev), "opacity_batch"));
   for (int k = 0; k < n_cond; ++k) c->cond_host[k] = CondArgs{T[k], P[k], q_ratio ? q_ratio[k] : o.q_ratio, 0.0};
-  const std::string key = batch_key(c, n_cond, mass, cut, g, o, kappa, tile);
+  const std::string key = batch_key(c, n_cond, mass, cut, g, o, kappa, shape);
   if (!c->gexec || c->gkey != key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -572,7 +585,7 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
                                          cudaMemcpyHostToDevice, c->stream),
                       "graph capture");
       if (st == HELK_OK) st = prepare_lines(c, n_cond, nullptr, mass, cut, g, o);
-      if (st == HELK_OK) st = run_voigt(c, n_cond, g, o, kappa, tile, ntiles);
+      if (st == HELK_OK) st = run_voigt(c, n_cond, g, o, kappa, shape, tile, ntiles);
       const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
       if (st == HELK_OK) st = cuda_check(c, e, "graph capture");
     }
@@ -896,10 +909,21 @@ int64_t helk_launch_count(const helk_ctx *c) { return c ? c->launches : -1; }
 
 int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max) {
   if (!out || (precision != HELK_PREC_F64 && precision != HELK_PREC_F32_KAHAN)) return 0;
-  int cand[16];
-  const int n = voigt_tile_candidates(precision, cand, 16);
+  int cand[32];
+  const int n = voigt_shape_candidates(precision, cand, 32);
   for (int i = 0; i < n && i < max; ++i) out[i] = cand[i];
   return n;
+}
+
+helk_status helk_tile_shape(int32_t precision, int32_t code, int32_t *points, int32_t *warps,
+                            int32_t *lines_per_stage) {
+  if (precision != HELK_PREC_F64 && precision != HELK_PREC_F32_KAHAN) return HELK_ERR_INVALID_ARG;
+  int p = 0, w = 0, l = 0;
+  if (!voigt_shape_info(precision, code, &p, &w, &l)) return HELK_ERR_INVALID_ARG;
+  if (points) *points = p;
+  if (warps) *warps = w;
+  if (lines_per_stage) *lines_per_stage = l;
+  return HELK_OK;
 }
 
 helk_status helk_set_tile(helk_ctx *c, int32_t precision, int64_t n, int32_t tile) {
@@ -913,8 +937,8 @@ helk_status helk_set_tile(helk_ctx *c, int32_t precision, int64_t n, int32_t til
     c->tuned_tile[prec] = 0;
     return HELK_OK;
   }
-  int cand[16];
-  const int nc = voigt_tile_candidates(precision, cand, 16);
+  int cand[32];
+  const int nc = voigt_shape_candidates(precision, cand, 32);
   bool ok = false;
   for (int i = 0; i < nc; ++i) ok = ok || cand[i] == tile;
   if (!ok) return set_err(c, HELK_ERR_INVALID_ARG, "set_tile: not a built tile shape");

@@ -288,27 +288,33 @@ cudaError_t launch_tilemap(helk_ctx *c, int n_cond, const helk_grid &g, int tile
 // Conditions ordered by decreasing evaluation count (largest work first).
 cudaError_t launch_cond_order(helk_ctx *c, int n_cond);
 // k_voigt.cu
-// Tile length (points per CTA) for a grid of n points: a multiple of the
-// kernel's block size chosen so that the tiles fill whole waves of resident
-// CTAs.
-int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n);
-// Tile lengths the autotuner times (points per CTA).
-int voigt_tile_candidates(int precision, int *out, int max);
+// Voigt kernel shapes.  A shape code names one built configuration of a
+// precision's kernel (FP32: the 1-based position in its shape list; FP64:
+// the slots per warp, 1..8).  voigt_shape_info gives the shape's tile
+// (points per CTA), warps per CTA and candidate lines per pipeline stage,
+// or returns false for an unknown code.
+bool voigt_shape_info(int precision, int code, int *points, int *warps, int *lines_per_stage);
+// The shape for a grid of n points (the tuned one, else one whose tile count
+// fills whole waves of resident CTAs).
+int voigt_shape(helk_ctx *c, int precision, int count, int64_t n);
+// Shape codes the autotuner times.
+int voigt_shape_candidates(int precision, int *out, int max);
 // Persistent Voigt kernel over n_cond x ntiles (condition, tile) items taken
 // from DevStats::tile_counter (reset to 0 before the launch); kappa of
 // condition k at kappa + k * g.n.
 cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
-                         double *kappa, int tile_len, int64_t ntiles);
+                         double *kappa, int shape, int64_t ntiles);
 // FP32 form: the Algorithm 916 cores that k_voigt_f32 leaves out, added into
 // kappa (launched after launch_voigt; no-op for the FP64 form).
 cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o);
 cudaError_t launch_core_add(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa);
 // k_voigt64.cu: the FP64 form (called by the dispatch above) and the
 // bounded-wait self-test
-int f64_tile_candidates(int *out, int max);
-int f64_tile_len(helk_ctx *c, int count, int64_t n);
+bool f64_shape_info(int code, int *points, int *warps, int *lines_per_stage);
+int f64_shape_candidates(int *out, int max);
+int f64_shape(helk_ctx *c, int count, int64_t n);
 cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa,
-                             int tile_len, int64_t ntiles);
+                             int shape, int64_t ntiles);
 cudaError_t launch_selftest_timeout(helk_ctx *c, int polls);
 // k_kdist.cu
 int64_t pinv_bytes(int64_t nb, int ncheb);

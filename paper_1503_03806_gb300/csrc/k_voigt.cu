@@ -592,91 +592,113 @@ cudaError_t launch_core_add(helk_ctx *c, int n_cond, const helk_grid &g, const h
 }
 
 // --------------------------------------------------------------- launch --
-constexpr int F32_BLOCK = 256, F32_LCH = 128;
+// FP32 kernel shapes, X(warps per CTA, slots per warp, candidate lines per
+// pipeline stage, resident CTAs per SM the kernel is compiled for); a shape's
+// code is its 1-based position in the list.  NSLOT is a template parameter
+// (no per-slot bounds test in the hot loops) and the tile is 32 warps NSLOT
+// points.  With 8 warps and 128-line stages the slots span 6..16, so that
+// the number of tiles can be matched to whole waves of resident CTAs (equal
+// tiles finish together, so a partial last wave idles the rest of the GPU);
+// the other entries vary the CTA size (4, 12 warps) and the stage length (64,
+// 256 lines) for the autotuner.
+#define HELK_F32_SHAPES(X)                                                                          \
+  X(8, 6, 128, 3) X(8, 7, 128, 3) X(8, 8, 128, 3) X(8, 9, 128, 2) X(8, 10, 128, 2) X(8, 11, 128, 2)   \
+  X(8, 12, 128, 2) X(8, 13, 128, 2) X(8, 14, 128, 2) X(8, 16, 128, 2) X(8, 8, 64, 3) X(8, 8, 256, 3)  \
+  X(8, 7, 256, 3) X(4, 8, 128, 6) X(4, 9, 128, 4) X(12, 8, 128, 2)
+constexpr int F32_COUNT_CODE = 3;  // the counting variant (statistics): 8 warps, 8 slots, 128 lines
+constexpr int F32_COUNT_NSLOT = 8, F32_COUNT_WARPS = 8, F32_COUNT_LCH = 128;
 
-// FP32 tiles: NSLOT is a template parameter (no per-slot bounds test in the
-// hot loops).  The tile is 256 NSLOT points; the choices span 6..16 slots so
-// that the number of tiles can be matched to whole waves of resident CTAs
-// (equal tiles finish together, so a partial last wave idles the rest of the
-// GPU).  X(NSLOT, resident CTAs per SM the kernel is compiled for).
-#define HELK_F32_NSLOTS(X) X(6, 3) X(7, 3) X(8, 3) X(9, 2) X(10, 2) X(11, 2) X(12, 2) X(13, 2) X(14, 2) X(16, 2)
-constexpr int F32_COUNT_NSLOT = 8;  // the counting variant (statistics) uses one tile shape
+struct F32Shape {
+  int warps, nslot, lch;
+};
+static const F32Shape kF32Shapes[] = {
+#define X(W, NS, L, MB) {W, NS, L},
+    HELK_F32_SHAPES(X)
+#undef X
+};
+constexpr int F32_NSHAPES = (int)(sizeof(kF32Shapes) / sizeof(kF32Shapes[0]));
 
-template <int NS, int MB>
+template <int W, int NS, int L, int MB>
 static int f32_slots(helk_ctx *c) {
-  return resident_ctas(c, k_voigt_f32<F32_BLOCK, NS, F32_LCH, false, MB>, F32_BLOCK);
+  return resident_ctas(c, k_voigt_f32<32 * W, NS, L, false, MB>, 32 * W);
 }
 
-int voigt_tile_candidates(int precision, int *out, int max) {
-  if (precision != HELK_PREC_F32_KAHAN) return f64_tile_candidates(out, max);
+bool voigt_shape_info(int precision, int code, int *points, int *warps, int *lines_per_stage) {
+  if (precision != HELK_PREC_F32_KAHAN) return f64_shape_info(code, points, warps, lines_per_stage);
+  if (code < 1 || code > F32_NSHAPES) return false;
+  const F32Shape &s = kF32Shapes[code - 1];
+  if (points) *points = 32 * s.warps * s.nslot;
+  if (warps) *warps = s.warps;
+  if (lines_per_stage) *lines_per_stage = s.lch;
+  return true;
+}
+
+int voigt_shape_candidates(int precision, int *out, int max) {
+  if (precision != HELK_PREC_F32_KAHAN) return f64_shape_candidates(out, max);
   int n = 0;
-#define X(NS, MB) \
-  if (n < max) out[n++] = F32_BLOCK * NS;
-  HELK_F32_NSLOTS(X)
-#undef X
+  for (int code = 1; code <= F32_NSHAPES && n < max; ++code) out[n++] = code;
   return n;
 }
 
-// Wave efficiency of ceil(n / (block p)) equal tiles on `slots` resident
-// CTAs, times the share of a (line, warp) pair's work that is evaluation
-// (the pair's fixed cost is about `setup` slots).
-static double f32_tile_score(int64_t n, int p, int slots) {
-  const int64_t ntiles = (n + (int64_t)F32_BLOCK * p - 1) / ((int64_t)F32_BLOCK * p);
+// Wave efficiency of ceil(n / tile) equal tiles on `slots` resident CTAs,
+// times the share of a (line, warp) pair's work that is evaluation (the
+// pair's fixed cost is about 2.5 slots).
+static double f32_tile_score(int64_t n, int tile, int p, int slots) {
+  const int64_t ntiles = (n + tile - 1) / tile;
   const double waves = (double)ntiles / slots;
   return waves / ceil(waves) * p / (p + 2.5);
 }
 
-int voigt_tile_len(helk_ctx *c, int precision, int count, int64_t n) {
+int voigt_shape(helk_ctx *c, int precision, int count, int64_t n) {
   const int prec = precision == HELK_PREC_F32_KAHAN ? 1 : 0;
   if (!count && c->tuned_tile[prec] > 0 && c->tuned_n[prec] == n) return c->tuned_tile[prec];
-  if (precision == HELK_PREC_F32_KAHAN) {
-    if (count) return F32_BLOCK * F32_COUNT_NSLOT;
-    int best = 8;
-    double best_score = -1.0;
-#define X(NS, MB)                                                 \
-    {                                                             \
-      const double sc = f32_tile_score(n, NS, f32_slots<NS, MB>(c)); \
-      if (sc > best_score + 1e-9) {                               \
-        best_score = sc;                                          \
-        best = NS;                                                \
-      }                                                           \
-    }
-    HELK_F32_NSLOTS(X)
-#undef X
-    return F32_BLOCK * best;
+  if (precision != HELK_PREC_F32_KAHAN) return f64_shape(c, count, n);
+  if (count) return F32_COUNT_CODE;
+  // without timing: the 8-warp, 128-line shapes by wave efficiency
+  int best = F32_COUNT_CODE, code = 0;
+  double best_score = -1.0;
+#define X(W, NS, L, MB)                                                                  \
+  ++code;                                                                                \
+  if (W == 8 && L == 128) {                                                              \
+    const double sc = f32_tile_score(n, 32 * W * NS, NS, f32_slots<W, NS, L, MB>(c));    \
+    if (sc > best_score + 1e-9) {                                                        \
+      best_score = sc;                                                                   \
+      best = code;                                                                       \
+    }                                                                                    \
   }
-  return f64_tile_len(c, count, n);
+  HELK_F32_SHAPES(X)
+#undef X
+  return best;
 }
 
 cudaError_t launch_voigt(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o,
-                         double *kappa, int tile_len, int64_t ntiles) {
+                         double *kappa, int shape, int64_t ntiles) {
   const int64_t nitems = ntiles * n_cond;
-  if (o.precision == HELK_PREC_F32_KAHAN) {
-    SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
-    const int ns = tile_len / F32_BLOCK;
-    if (o.count_regions) {
-      if (ns != F32_COUNT_NSLOT) return cudaErrorInvalidValue;
-      auto kern = k_voigt_f32<F32_BLOCK, F32_COUNT_NSLOT, F32_LCH, true, 3>;
-      ++c->launches;
-      kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(
-          c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, o.weight,
-          o.accumulate, kappa, c->cstats, c->stats, sq);
-      return cudaGetLastError();
-    }
-#define X(NS, MB)                                                                                 \
-    if (ns == NS) {                                                                               \
-      auto kern = k_voigt_f32<F32_BLOCK, NS, F32_LCH, false, MB>;                                  \
-      ++c->launches;                                                                               \
-      kern<<<persistent_grid(c, kern, F32_BLOCK, nitems), F32_BLOCK, 0, c->stream>>>(              \
-          c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n,    \
-          o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                                 \
-      return cudaGetLastError();                                                                  \
-    }
-    HELK_F32_NSLOTS(X)
-#undef X
-    return cudaErrorInvalidValue;
+  if (o.precision != HELK_PREC_F32_KAHAN) return launch_voigt_f64(c, n_cond, g, o, kappa, shape, ntiles);
+  SurrQueue *sq = o.surrogate ? c->squeue : nullptr;
+  if (o.count_regions) {
+    if (shape != F32_COUNT_CODE) return cudaErrorInvalidValue;
+    constexpr int B = 32 * F32_COUNT_WARPS;
+    auto kern = k_voigt_f32<B, F32_COUNT_NSLOT, F32_COUNT_LCH, true, 3>;
+    ++c->launches;
+    kern<<<persistent_grid(c, kern, B, nitems), B, 0, c->stream>>>(
+        c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n, o.weight,
+        o.accumulate, kappa, c->cstats, c->stats, sq);
+    return cudaGetLastError();
   }
-  return launch_voigt_f64(c, n_cond, g, o, kappa, tile_len, ntiles);
+  int code = 0;
+#define X(W, NS, L, MB)                                                                           \
+  if (++code == shape) {                                                                          \
+    auto kern = k_voigt_f32<32 * W, NS, L, false, MB>;                                             \
+    ++c->launches;                                                                                 \
+    kern<<<persistent_grid(c, kern, 32 * W, nitems), 32 * W, 0, c->stream>>>(                      \
+        c->rec32, c->nlines, c->tile_lo, c->tile_hi, ntiles, c->cond_order, n_cond, (int)g.n,      \
+        o.weight, o.accumulate, kappa, c->cstats, c->stats, sq);                                   \
+    return cudaGetLastError();                                                                    \
+  }
+  HELK_F32_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace helk

@@ -243,24 +243,35 @@ static int pick_nslot(int64_t n, int block, int ppt, int slots) {
   return best;
 }
 
-int f64_tile_candidates(int *out, int max) {
+// FP64 shapes: the code is the slots per warp (1..F64_PPT) of 8-warp CTAs
+// with 64-line stages; the autotuner times 4, 6 and 8.
+bool f64_shape_info(int code, int *points, int *warps, int *lines_per_stage) {
+  if (code < 1 || code > F64_PPT) return false;
+  if (points) *points = F64_BLOCK * code;
+  if (warps) *warps = F64_BLOCK / 32;
+  if (lines_per_stage) *lines_per_stage = F64_LCH;
+  return true;
+}
+
+int f64_shape_candidates(int *out, int max) {
   int n = 0;
   const int f64_choices[] = {4, 6, 8};
   for (int p : f64_choices)
-    if (n < max) out[n++] = F64_BLOCK * p;
+    if (n < max) out[n++] = p;
   return n;
 }
 
-int f64_tile_len(helk_ctx *c, int count, int64_t n) {
+int f64_shape(helk_ctx *c, int count, int64_t n) {
   const int slots = count ? resident_ctas(c, k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true>, F64_BLOCK)
                           : resident_ctas(c, k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, false>, F64_BLOCK);
-  return F64_BLOCK * pick_nslot(n, F64_BLOCK, F64_PPT, slots);
+  return pick_nslot(n, F64_BLOCK, F64_PPT, slots);
 }
 
 cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa,
-                             int tile_len, int64_t ntiles) {
+                             int shape, int64_t ntiles) {
   const int64_t nitems = ntiles * n_cond;
-  const int nslot = tile_len / F64_BLOCK;
+  const int nslot = shape;
+  if (nslot < 1 || nslot > F64_PPT) return cudaErrorInvalidValue;
   if (o.count_regions) {
     auto kern = k_voigt_f64<F64_BLOCK, F64_PPT, F64_LCH, true>;
     ++c->launches;

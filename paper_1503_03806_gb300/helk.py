@@ -85,6 +85,7 @@ SIGNATURES = [
                                      ctypes.POINTER(helk_grid), ctypes.POINTER(helk_opts),
                                      ctypes.POINTER(_I32)]),
     ("helk_tile_candidates", _I32, [_I32, _P, _I32]),
+    ("helk_tile_shape", ctypes.c_int, [_I32, _I32, _P, _P, _P]),
     ("helk_launch_count", _I64, [_P]),
     ("helk_set_tile", ctypes.c_int, [_P, _I32, _I64, _I32]),
 ]
@@ -184,10 +185,20 @@ def helk_stage_times(ctx):
 
 # -------------------------------------------------------------- Context --
 def helk_tile_candidates(precision):
-    """The built Voigt tile shapes (points per CTA tile) of a precision."""
+    """The shape codes of a precision's Voigt kernel that the autotuner times."""
     out = (_I32 * 32)()
     n = lib.helk_tile_candidates(int(precision), out, 32)
     return [int(out[i]) for i in range(min(n, 32))]
+
+
+def helk_tile_shape(precision, code):
+    """A shape code decoded: {"points": per CTA tile, "warps": per CTA,
+    "lines_per_stage": candidate lines per pipeline stage}."""
+    p, w, l = _I32(0), _I32(0), _I32(0)
+    st = lib.helk_tile_shape(int(precision), int(code), ctypes.byref(p), ctypes.byref(w), ctypes.byref(l))
+    if st != HELK_OK:
+        raise HelkError(st, "tile_shape: unknown precision or shape code %r" % (code,))
+    return {"points": int(p.value), "warps": int(w.value), "lines_per_stage": int(l.value)}
 
 
 def _cut(cut):
@@ -323,8 +334,9 @@ class Context:
         return ev, (reg if with_regions else None)
 
     def autotune(self, T, P, mass, cut, grid, precision=HELK_PREC_F64, q_ratio=1.0):
-        """Time the built Voigt tile shapes on this condition; keep the
-        fastest for later calls with the same precision and grid size."""
+        """Time the candidate Voigt kernel shapes on this condition; keep the
+        fastest for later calls with the same precision and grid size.
+        Returns its shape code (helk_tile_shape decodes it)."""
         g = helk_grid(float(grid[0]), float(grid[1]), int(grid[2]))
         o = helk_opts(int(precision), 0, 1.0, float(q_ratio), 0, 0)
         t = _I32(0)
@@ -337,7 +349,8 @@ class Context:
         return int(lib.helk_launch_count(self.h))
 
     def set_tile(self, precision, n, tile):
-        """Fix the Voigt tile shape for grids of n points (0: built-in choice)."""
+        """Fix the Voigt kernel shape (a code from helk_tile_candidates) for
+        grids of n points (0: built-in choice)."""
         _check(self.h, lib.helk_set_tile(self.h, int(precision), int(n), int(tile)))
 
     # ------------------------------------------------------ surrogate --

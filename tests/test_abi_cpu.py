@@ -56,6 +56,25 @@ def test_null_arguments_are_rejected_without_a_gpu(helk):
     lib.helk_destroy(None)
 
 
+def test_kernel_shapes_decode_without_a_gpu(helk):
+    # the autotuner's dimensions: tile width (slots per warp), warps per CTA
+    # and candidate lines per pipeline stage, each shape named by its code
+    f32 = helk.helk_tile_candidates(helk.HELK_PREC_F32_KAHAN)
+    shapes = [helk.helk_tile_shape(helk.HELK_PREC_F32_KAHAN, c) for c in f32]
+    assert len(set(f32)) == len(f32) >= 10
+    assert {s["warps"] for s in shapes} >= {4, 8, 12}
+    assert {s["lines_per_stage"] for s in shapes} >= {64, 128, 256}
+    assert len({s["points"] for s in shapes if s["warps"] == 8 and s["lines_per_stage"] == 128}) >= 8
+    for s in shapes:
+        assert s["points"] % (32 * s["warps"]) == 0
+    f64 = helk.helk_tile_candidates(helk.HELK_PREC_F64)
+    assert [helk.helk_tile_shape(helk.HELK_PREC_F64, c)["points"] for c in f64] == [256 * c for c in f64]
+    for prec, bad in ((helk.HELK_PREC_F32_KAHAN, 0), (helk.HELK_PREC_F32_KAHAN, len(f32) + 1),
+                      (helk.HELK_PREC_F64, 9), (7, 1)):
+        with pytest.raises(helk.HelkError):
+            helk.helk_tile_shape(prec, bad)
+
+
 def test_create_without_gpu_returns_status():
     import torch
     if torch.cuda.is_available():

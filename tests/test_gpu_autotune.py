@@ -1,7 +1,8 @@
-"""The Voigt tile shapes and their autotuner: every built shape gives the
-same FP64 result bit for bit (every grid point sums its lines in list order
+"""The Voigt kernel shapes and their autotuner: every candidate shape (tile
+width, warps per CTA, candidate lines per pipeline stage) gives the same
+FP64 result bit for bit (every grid point sums its lines in list order
 whatever the tiling) and the same FP32 result up to rounding; the autotuner
-picks one of the built shapes and keeps the results."""
+picks one of the candidates and keeps the results."""
 import numpy as np
 import pytest
 
