@@ -94,21 +94,18 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
-// Makes room for n more lines in the plain partials: when the group would
-// exceed KAHAN_GROUP lines, Kahan-adds the partials into (sum, comp) and
-// starts a new group.
+// Kahan-adds the plain partials into (sum, comp) and starts a new group.
+// The loops over a group's lines run in stretches that end where the group
+// is full, so the check is made once per stretch, not once per line.
 template <int NSLOT>
-__device__ __forceinline__ void kahan_room(int &ngroup, int n, float (&sum)[NSLOT], float (&comp)[NSLOT],
+__device__ __forceinline__ void kahan_fold(int &ngroup, float (&sum)[NSLOT], float (&comp)[NSLOT],
                                            float (&part)[NSLOT]) {
-  if (ngroup + n > KAHAN_GROUP) {
-    ngroup = 0;
+  ngroup = 0;
 #pragma unroll
-    for (int k = 0; k < NSLOT; ++k) {
-      kahan_add(sum[k], comp[k], part[k]);
-      part[k] = 0.0f;
-    }
+  for (int k = 0; k < NSLOT; ++k) {
+    kahan_add(sum[k], comp[k], part[k]);
+    part[k] = 0.0f;
   }
-  ngroup += n;
 }
 
 // 3-node Gauss-Hermite (nodes 0, +-t, t^2 = 3/2, weights 4 w1, w1):
@@ -395,84 +392,96 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     }
     __syncwarp();
     // whole-span GH1 lines: 5 instructions an evaluation
-    for (int t = 0; t < n1; ++t) {
-      const WarpLine &W = wl[t];
-      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
-      const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2, P1 = W.q0;
-#pragma unroll
-      for (int k = 0; k < NSLOT; ++k) {
-        const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-        part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
-      }
-      if (COUNT) cnt[2] += NSLOT;
-    }
-    // whole-span GH3 lines: 10 instructions an evaluation
-    for (int t = n1; t < n13; ++t) {
-      const WarpLine &W = wl[t];
-      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
-      const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2;
-      const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
-#pragma unroll
-      for (int k = 0; k < NSLOT; ++k) {
-        const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-        part[k] = g3.add(part[k], fmaf(u, u, a2));
-      }
-      if (COUNT) cnt[1] += NSLOT;
-    }
-    // the rest: GH1 or GH3 lines covering part of the span, and lines with a
-    // method boundary or their core in the span
-    for (int jj = n13; jj < nall; ++jj) {
-      const WarpLine &W = wl[jj];
-      const int cls = W.code & 3;
-      kahan_room<NSLOT>(ngroup, 1, sum, comp, part);
-      const int lo = W.lo, hi = W.hi;
-      const float beta = W.beta, nphi = W.nphi, a2 = W.a2;
-      // (i - c) of this lane's first point, exact in FP32
-      const float d0 = W.d0 + lanef;
-      if (cls == CLS_GH1) {
-        const float P1 = W.q0;
+    for (int t = 0; t < n1;) {
+      const int te = min(n1, t + KAHAN_GROUP - ngroup);
+      ngroup += te - t;
+      for (; t < te; ++t) {
+        const WarpLine &W = wl[t];
+        const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2, P1 = W.q0;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
-          const int i = wbase + lane + 32 * k;
           const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-          const float r2 = fmaf(u, u, a2);
-          const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
-          part[k] += in ? P1 * fast_rcp(r2) : 0.0f;
-          if (COUNT) cnt[2] += in;
+          part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
         }
-      } else if (cls == CLS_GH3) {
+        if (COUNT) cnt[2] += NSLOT;
+      }
+      if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
+    }
+    // whole-span GH3 lines: 10 instructions an evaluation
+    for (int t = n1; t < n13;) {
+      const int te = min(n13, t + KAHAN_GROUP - ngroup);
+      ngroup += te - t;
+      for (; t < te; ++t) {
+        const WarpLine &W = wl[t];
+        const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2;
         const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
-          const int i = wbase + lane + 32 * k;
           const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-          const float r2 = fmaf(u, u, a2);
-          const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
-          part[k] = in ? g3.add(part[k], r2) : part[k];
-          if (COUNT) cnt[1] += in;
+          part[k] = g3.add(part[k], fmaf(u, u, a2));
         }
-      } else {
-        // Per point: GH1 or GH3; core points (r^2 < 100) are left to the
-        // core kernel, which evaluates them after this one.
-        const int j = W.j;
-        const float P1 = W.q0;
-        const Gh3Line g3(a2, buf[j].P3);
+        if (COUNT) cnt[1] += NSLOT;
+      }
+      if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
+    }
+    // the rest: GH1 or GH3 lines covering part of the span, and lines with a
+    // method boundary or their core in the span
+    for (int jj = n13; jj < nall;) {
+      const int je = min(nall, jj + KAHAN_GROUP - ngroup);
+      ngroup += je - jj;
+      for (; jj < je; ++jj) {
+        const WarpLine &W = wl[jj];
+        const int cls = W.code & 3;
+        const int lo = W.lo, hi = W.hi;
+        const float beta = W.beta, nphi = W.nphi, a2 = W.a2;
+        // (i - c) of this lane's first point, exact in FP32
+        const float d0 = W.d0 + lanef;
+        if (cls == CLS_GH1) {
+          const float P1 = W.q0;
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-          const int i = wbase + lane + 32 * k;
-          if ((unsigned)(i - lo) <= (unsigned)(hi - lo)) {
+          for (int k = 0; k < NSLOT; ++k) {
+            const int i = wbase + lane + 32 * k;
             const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
             const float r2 = fmaf(u, u, a2);
-            if (r2 >= 1.0e6f) {
-              part[k] = fmaf(P1, fast_rcp(r2), part[k]);
-              if (COUNT) cnt[2]++;
-            } else if (r2 >= 100.0f) {
-              part[k] = g3.add(part[k], r2);
-              if (COUNT) cnt[1]++;
+            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+            part[k] += in ? P1 * fast_rcp(r2) : 0.0f;
+            if (COUNT) cnt[2] += in;
+          }
+        } else if (cls == CLS_GH3) {
+          const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const int i = wbase + lane + 32 * k;
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            const bool in = (unsigned)(i - lo) <= (unsigned)(hi - lo);
+            part[k] = in ? g3.add(part[k], r2) : part[k];
+            if (COUNT) cnt[1] += in;
+          }
+        } else {
+          // Per point: GH1 or GH3; core points (r^2 < 100) are left to the
+          // core kernel (k_core_f32).
+          const int j = W.j;
+          const float P1 = W.q0;
+          const Gh3Line g3(a2, buf[j].P3);
+#pragma unroll
+          for (int k = 0; k < NSLOT; ++k) {
+            const int i = wbase + lane + 32 * k;
+            if ((unsigned)(i - lo) <= (unsigned)(hi - lo)) {
+              const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+              const float r2 = fmaf(u, u, a2);
+              if (r2 >= 1.0e6f) {
+                part[k] = fmaf(P1, fast_rcp(r2), part[k]);
+                if (COUNT) cnt[2]++;
+              } else if (r2 >= 100.0f) {
+                part[k] = g3.add(part[k], r2);
+                if (COUNT) cnt[1]++;
+              }
             }
           }
         }
       }
+      if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
     }
     __syncwarp();  // the group's records are overwritten next
     }
