@@ -387,10 +387,12 @@ static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single
 }
 
 // Tile map, condition order and the persistent Voigt kernel.
-// Points per CTA tile of a shape code returned by voigt_shape or the candidates.
+// Points per CTA tile of a shape code returned by voigt_shape or the
+// candidates (codes that always decode; 0 would mean a logic error, which
+// launch_voigt then reports as an invalid launch).
 static int shape_points(int precision, int shape) {
   int p = 0;
-  return voigt_shape_info(precision, shape, &p, nullptr, nullptr) ? p : 1;
+  return voigt_shape_info(precision, shape, &p, nullptr, nullptr) ? p : 0;
 }
 
 // `shape`: the Voigt kernel's shape code; `tile`: its points per CTA tile.
@@ -435,6 +437,7 @@ helk_status helk_opacity(helk_ctx *c, double T, double P, double mass, const hel
   }
   const int shape = voigt_shape(c, o.precision, o.count_regions, g->n);
   const int tile = shape_points(o.precision, shape);
+  if (tile <= 0) return set_err(c, HELK_ERR_STATE, "opacity: no kernel shape");
   const int64_t ntiles = (g->n + tile - 1) / tile;
   HELK_TRY(ensure_call_buffers(c, 1, o, ntiles, g->n));
   const CondArgs one{T, P, o.q_ratio, 0.0};
@@ -472,7 +475,7 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   const int ncand = voigt_shape_candidates(o.precision, cand, 32);
   int64_t max_tiles = 0;
   for (int i = 0; i < ncand; ++i) {
-    const int pts = shape_points(o.precision, cand[i]);
+    const int pts = std::max(1, shape_points(o.precision, cand[i]));
     max_tiles = std::max(max_tiles, (g->n + pts - 1) / pts);
   }
   HELK_TRY(ensure_call_buffers(c, 1, o, max_tiles, g->n));
@@ -488,7 +491,7 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
   int best = cand[0];
   helk_status st = HELK_OK;
   for (int i = 0; i < ncand && st == HELK_OK; ++i) {
-    const int pts = shape_points(o.precision, cand[i]);
+    const int pts = std::max(1, shape_points(o.precision, cand[i]));
     const int64_t ntiles = (g->n + pts - 1) / pts;
     st = run_voigt(c, 1, g, o, c->kappa, cand[i], pts, ntiles);  // warm-up
     float ms = 0.f;
@@ -561,6 +564,7 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
   }
   const int shape = voigt_shape(c, o.precision, o.count_regions, g->n);
   const int tile = shape_points(o.precision, shape);
+  if (tile <= 0) return set_err(c, HELK_ERR_STATE, "opacity: no kernel shape");
   const int64_t ntiles = (g->n + tile - 1) / tile;
   HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles, g->n));
   if (!c->cap_stream)

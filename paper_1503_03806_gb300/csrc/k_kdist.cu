@@ -410,6 +410,7 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
 // more than KD_BUCKET_MAX keys this returns false with A untouched, and the
 // caller radix-sorts instead.
 constexpr int KD_NBUCKET = KD_THREADS * 8;  // block_exscan_4096's counters
+static_assert((KD_THREADS & (KD_THREADS - 1)) == 0, "the key order of the bucket passes needs a power of 2");
 constexpr int KD_BUCKET_MAX = 512;
 
 __device__ __forceinline__ int hpad(int b) { return b + (b >> 4); }  // block_exscan_4096's layout
