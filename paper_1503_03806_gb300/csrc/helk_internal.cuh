@@ -189,7 +189,7 @@ struct helk_ctx {
   // generic upload scratch
   void *tmp = nullptr;
   int64_t tmp_cap = 0;
-  // autotuned Voigt tile length per precision (0 = heuristic), valid for
+  // autotuned Voigt kernel shape code per precision (0 = heuristic), valid for
   // grids of tuned_n points
   int tuned_tile[2] = {0, 0};
   int64_t tuned_n[2] = {0, 0};

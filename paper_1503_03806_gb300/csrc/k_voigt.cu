@@ -1,10 +1,12 @@
 // k_voigt.cu -- the FP32 form of the line-tiled Voigt opacity kernel
 // (Sec. 2.3-2.5): FP32 profile evaluation on records with strengths scaled by
 // 2^-E, Kahan-compensated FP32 accumulation per point, the result converted
-// to FP64 and rescaled at the flush; and the precision dispatch of the Voigt
-// launch.  Persistent CTAs; warp w of a tile owns 32 NSLOT consecutive grid
-// points; the candidate lines of successive tiles stream through a
-// shared-memory ring filled by 1-D bulk copies (see the pipeline below).
+// to FP64 and rescaled at the flush; its Algorithm 916 cores in a separate
+// kernel that runs beside it on a second stream; the table of kernel shapes
+// the autotuner times; and the precision dispatch of the Voigt launch.
+// Persistent CTAs; warp w of a tile owns 32 NSLOT consecutive grid points;
+// the candidate lines of successive tiles stream through a shared-memory
+// ring filled by 1-D bulk copies (see the pipeline below).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
