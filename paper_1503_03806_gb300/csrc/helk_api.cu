@@ -386,16 +386,17 @@ static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single
   return HELK_OK;
 }
 
-// Tile map, condition order and the persistent Voigt kernel.
 // Points per CTA tile of a shape code returned by voigt_shape or the
 // candidates (codes that always decode; 0 would mean a logic error, which
-// launch_voigt then reports as an invalid launch).
+// the callers report).
 static int shape_points(int precision, int shape) {
   int p = 0;
   return voigt_shape_info(precision, shape, &p, nullptr, nullptr) ? p : 0;
 }
 
-// `shape`: the Voigt kernel's shape code; `tile`: its points per CTA tile.
+// Tile map, condition order and the persistent Voigt kernel (for the FP32
+// form with its Algorithm 916 cores).  `shape`: the Voigt kernel's shape
+// code; `tile`: its points per CTA tile.
 static helk_status run_voigt(helk_ctx *c, int n_cond, const helk_grid *g, const helk_opts &o, double *kappa,
                              int shape, int tile, int64_t ntiles) {
   HELK_TRY(cuda_check(c, launch_tilemap(c, n_cond, *g, tile, ntiles), "tilemap"));
