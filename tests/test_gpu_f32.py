@@ -95,6 +95,21 @@ def test_medium_workload_whole_bins(ctx):
     check_binned(k[idx], ko, len(bins), "medium workload bins %s" % bins)
 
 
+@pytest.mark.parametrize("P,ngrid", [(1e-7, 2048 + 5), (0.02, 1), (100.0, 33), (3000.0, 2048 + 5)])
+def test_pressure_extremes_and_tiny_grids(ctx, P, ngrid):
+    # 1e-7 atm: Doppler cores, no wings to speak of; 0.02 atm: a < 10, cores
+    # beside GH3 wings; 100 and 3000 atm: a^2 >= 1e6 for most lines, so whole
+    # spans that hold the line centre are GH1 (or GH3) without a core; grids
+    # of 1, 33 and 2053 points (one ragged tile)
+    lines = synth.random_lines(500, 404, 40.0, 60.0)
+    case = Case(1200.0, P, 18.0, (49.0, 0.001, ngrid), ("abs", 10.0))
+    ctx.upload(lines)
+    k = f32(ctx, case)
+    ko, _, _ = oracle.opacity(lines, case.oracle_cond(), nthreads=NTHREADS)
+    assert np.all(np.isfinite(k)) and np.all(k >= 0.0)
+    check_binned(k, ko, 1, "P=%g, %d points" % (P, ngrid))
+
+
 def test_extreme_strength_range(ctx):
     # strengths over 40 decades: the FP32 form rescales by the largest S'
     rng = np.random.default_rng(5)
