@@ -281,7 +281,7 @@ helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
  *   f1 = 2 asinh|x| / asinh(10) - 1,  f2 = 2 (log10 y + 4) / 5 - 1,
  * for 1e-4 <= y < 10.  Parameters: 8577 floats, W1[2][64], b1[64],
  * W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4 (W[in][out]).
- * Training targets are this library's FP64 Algorithm 916; the same judges
+ * Training targets are this library's FP64 Algorithm 916; the same checks
  * the network cell by cell (helk_surrogate_validate), and only validated
  * cells are routed to it (helk_opts.surrogate).
  * ------------------------------------------------------------------- */

@@ -13,7 +13,7 @@
 // ~2^-16 per product) in FP32; the 2 -> 64 input layer and the 64 -> 1 output
 // layer run in FP32 on the CUDA cores.  The backward pass uses plain BF16
 // MMAs.  Training targets come from this library's FP64 Algorithm 916
-// (itself held to the oracle at 1e-9), which also judges the network on a
+// (itself held to the oracle at 1e-9), which also checks the network on a
 // held-out lattice; the network is used only in the cells where that check
 // passed.
 //
@@ -471,7 +471,7 @@ __global__ void k_mlp_samples(int64_t n, uint64_t seed, float *__restrict__ feat
   }
 }
 
-// Algorithm 916 (FP64) at given points: the judge of the network.
+// Algorithm 916 (FP64) at given points: the reference the network is checked against.
 __global__ void k_a916_points(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                               double *__restrict__ kout) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
