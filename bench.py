@@ -77,6 +77,19 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def kdist_hbm(ms, n, peaks):
+    """HBM view of the k-table stage: its algorithmic bytes (each opacity
+    read once, 8 B a point; the pseudo-inverse comes from L2) over its time,
+    against the measured copy bandwidth."""
+    if not ms:
+        return None
+    gbs = 8.0 * n / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    return {"bytes_per_launch": 8 * n, "achieved": gbs, "unit": "GB/s", "peak": peak,
+            "frac": gbs / peak if peak else None,
+            "note": "latency-bound per-bin sort and fit, one CTA per bin; not HBM-bound at 1e4-point bins"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -510,6 +523,7 @@ def run_ours(args):
                           "evals_by_method": {"alg916": reg[0], "gh3": reg[1], "gh1": reg[2]}},
                "rel_err_f32_vs_f64": err32,
                "stages_ms_per_step": r32["stages"],
+               "kdist_hbm": kdist_hbm(r32["stages"].get("kdist"), grid[2], peaks),
                "roofline": r32["roofline"], "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "gpu_launches": r32["launches"],
                "fp64": {"value": r64["value"], "ms_per_step": r64["ms_step"],
