@@ -133,7 +133,7 @@ struct helk_ctx {
   int64_t core_cap = 0;
   double *ckey = nullptr;
   int64_t ckey_cap = 0;
-  int32_t *ckey32 = nullptr;  // FP32 form: ckey clamped to +-2e9 (order kept), for integer searches
+  int32_t *ckey32 = nullptr;  // FP32 form: ckey clamped to the int32 range (order kept), for integer searches
   int64_t ckey32_cap = 0;
   // FP32 form: the core kernel runs on side_stream beside the main Voigt
   // kernel and leaves its per-point sums in kcore (FP32, n_cond x n points)

@@ -405,7 +405,7 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // decades below it); the centre as the integer grid index c plus the FP32
 // offset phi = (nu0' - nu_c) ku, so that u_i = (i - c) beta - phi keeps full
 // relative precision near the line centre.
-__global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu,
+__global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu, int64_t ngrid,
                          const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
                          int2 *__restrict__ core_all, int32_t *__restrict__ ckey32) {
   const int cond = blockIdx.y;
@@ -422,13 +422,17 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
        l += (int64_t)gridDim.x * blockDim.x) {
     const LineRec64 r = r64[l];
     const double key = ckey[l];
-    if (cond == 0) ckey32[l] = (int32_t)fmin(fmax(key, -2.0e9), 2.0e9);
+    if (cond == 0) ckey32[l] = (int32_t)fmin(fmax(key, -2147483647.0), 2147483647.0);
     LineRec32 q;
     // any integer within a step of the centre serves as c (phi takes the
     // rest), so a product by 1/dnu replaces the division
+    // (clamped to the grid, [0, ngrid - 1]: exact for every centre on the
+    // grid, and i - c then fits in 32 bits for every grid index i; a centre
+    // off the grid leaves its offset in phi, which has the sign of i - c, so
+    // u = (i - c) beta - phi takes no cancellation)
     double cf = rint((r.nu0p - nu_min) * idnu);
-    if (cf < -1.0e9) cf = -1.0e9;
-    if (cf > 1.0e9) cf = 1.0e9;
+    if (cf < 0.0) cf = 0.0;
+    if (cf > (double)(ngrid - 1)) cf = (double)(ngrid - 1);
     q.c = (int32_t)cf;
     q.ilo = r.ilo;
     q.ihi = r.ihi;
@@ -479,7 +483,7 @@ cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
   ++c->launches;
-  k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, c->ckey, c->cstats, c->rec32,
+  k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, g.n, c->ckey, c->cstats, c->rec32,
                                         c->core_rng, c->ckey32);
   return cudaGetLastError();
 }

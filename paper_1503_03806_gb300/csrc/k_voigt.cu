@@ -224,7 +224,7 @@ __device__ void f32_drain(F32Pipe &P, int *flags) {
 struct __align__(16) WarpLine {
   int code;          // 0: the line misses the warp; else class | full << 2
   int lo, hi;        // covered points (grid indices)
-  float d0;          // (float)(wbase - c), exact
+  float d0;          // (float)(wbase - c): exact within 2^24 points of c
   float beta, nphi, a2;
   float q0, q1, q2, q3;  // GH1: P1; GH3: C, c3, c45, c2 (Gh3Line); mixed: P1
   int j;             // the line's index in the chunk
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256)
   const double scale = ldexp(weight, cst[cond].scale_exp);
   const float *kcore = kcore_all + (int64_t)cond * ngrid;
   double *kappa = kappa_all + (int64_t)cond * ngrid;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ngrid; i += gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ngrid; i += (int64_t)gridDim.x * blockDim.x) {
     const float v = kcore[i];
     if (v != 0.0f) kappa[i] += scale * (double)v;
   }

@@ -10,6 +10,9 @@ computes one by one.
 - mixed: 4 species x 2.5e7 lines (masses 18, 16, 44, 17 amu, mixing 1/4
   each) in one upload with per-line mass and abundance weight, on the 3e7
   point grid at 0.001 cm^-1; one condition in the FP32 form.
+- the largest grid accepted (2^31 - 4097 points), both forms: lines at both
+  ends and beyond index 2^30, and, without a cutoff, lines whose centres lie
+  outside the int32 range of grid indices.
 
 The oracle sums every line of the list whose window holds the point.  For
 the 1e8-line list it is given, per sampled region, the lines whose centre
@@ -85,6 +88,70 @@ def test_tp_grid_batches(ctx):
         assert sel.sum() > 0
         err = np.abs(k32[c][idx][sel] - ko[sel]) / ko[sel]
         assert err.max() <= RTOL32, ("tp_grid FP32 condition %d" % c, err.max())
+
+
+NMAX = 2**31 - 1 - 4096  # the largest grid the library accepts
+
+
+def _region_idx(centres, halfwidth, n):
+    idx = np.concatenate([np.arange(max(0, c - halfwidth), min(n, c + halfwidth + 1)) for c in centres])
+    return np.unique(idx)
+
+
+def _check_points(k_dev, idx, ko, rtol, floor, what):
+    """Compare the device result at idx (a gather on the device) with the
+    oracle: every point for rtol 1e-9, else points above floor x max."""
+    import torch
+    got = k_dev[torch.from_numpy(idx).cuda()].cpu().numpy()
+    sel = (ko > floor * ko.max()) & (ko > 0) if floor else ko != 0
+    assert sel.sum() > 0, what
+    err = np.abs(got[sel] - ko[sel]) / ko[sel]
+    assert err.max() <= rtol, (what, float(err.max()))
+    assert np.all(got[ko == 0] == 0.0), what
+
+
+def test_largest_grid(ctx):
+    # 2^31 - 4097 points (the largest grid accepted): line centres near both
+    # ends and at index ~1.5e9, windows of 50 points (Algorithm 916 cores near
+    # the end, where the Doppler width is large; GH1 wings near the start);
+    # then, without a cutoff, lines whose centres lie far outside the grid on
+    # both sides (beyond the int32 range of grid indices) reach every point
+    import torch
+    from paper_1503_03806_gb300 import helk
+    n, dnu = NMAX, 0.001
+    rng = np.random.default_rng(77)
+    end = (n - 1) * dnu
+    nu = np.sort(np.concatenate([rng.uniform(0.02, 0.06, 6), rng.uniform(1.5e6, 1.5e6 + 0.04, 6),
+                                 rng.uniform(end - 0.05, end + 0.01, 6)]))
+    lines = {"nu0": nu, "S0": 10.0 ** rng.uniform(-24, -20, nu.size), "gamma_air": rng.uniform(0.02, 0.1, nu.size)}
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    case = Case(1500.0, 1.0, 18.0, (0.0, dnu, n), ("abs", 0.05))
+    ctx.upload(lines)
+    cidx = np.rint(nu / dnu).astype(np.int64)
+    idx = _region_idx(cidx, 80, n)
+    ko, evo = oracle.opacity_points(lines, case.oracle_cond(), idx)
+    case.gpu(ctx, out=out, count_regions=True)
+    ev, reg = ctx.stats(with_regions=True)
+    _check_points(out, idx, ko, 1e-9, 0.0, "largest grid FP64")
+    assert reg[0] > 0 and reg[2] > 0  # Algorithm 916 and GH1 both used
+    case.gpu(ctx, out=out, precision=helk.HELK_PREC_F32_KAHAN)
+    _check_points(out, idx, ko, 1e-5, 1e-8, "largest grid FP32")
+    assert float(out[-1]) > 0.0 and float(out[0]) > 0.0
+    # no cutoff: two lines inside, two far outside (grid starts at 3e6 cm^-1)
+    nu2 = np.array([10.0, 3.0e6 + 0.03, 3.0e6 + end - 0.02, 9.0e6])
+    lines2 = {"nu0": nu2, "S0": np.array([1e-20, 1e-22, 1e-22, 1e-20]),
+              "gamma_air": np.array([0.05, 0.07, 0.03, 0.08])}
+    case2 = Case(1500.0, 1.0, 18.0, (3.0e6, dnu, n), ("none",))
+    ctx.upload(lines2)
+    idx2 = np.unique(np.concatenate([_region_idx([30, n - 20], 60, n),
+                                     rng.integers(0, n, 200), [0, n - 1]]))
+    ko2, _ = oracle.opacity_points(lines2, case2.oracle_cond(), idx2)
+    case2.gpu(ctx, out=out)
+    _check_points(out, idx2, ko2, 1e-9, 0.0, "largest grid, no cutoff, FP64")
+    case2.gpu(ctx, out=out, precision=helk.HELK_PREC_F32_KAHAN)
+    _check_points(out, idx2, ko2, 1e-5, 1e-8, "largest grid, no cutoff, FP32")
+    del out
+    torch.cuda.empty_cache()
 
 
 def test_mixed_species_full_size(ctx):
