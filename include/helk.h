@@ -207,7 +207,9 @@ helk_status helk_opacity_stats(helk_ctx *ctx, int64_t *n_evals,
  * else device memory.  kg_out: optional device pointer to n doubles that
  * receives the sorted values.  1 <= ncheb <= 32, ncheb <= N_b.
  * The sorted values equal those of any correct ascending sort, bit for
- * bit. */
+ * bit.  kappa holds non-negative values, as helk_opacity writes them (the
+ * sort orders the IEEE bit patterns); for negative or NaN values the tables
+ * are unspecified (an infinite or NaN largest value gives that mean). */
 helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
                        int32_t nbins, int32_t ncheb, double kappa_floor,
                        double *coeffs, double *mean, int32_t out_on_host,
