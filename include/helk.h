@@ -4,10 +4,10 @@
  * Method: Grimm & Heng 2015, "HELIOS-K: an ultrafast, open-source opacity
  * calculator for radiative transfer" (arXiv:1503.03806).
  *   Opacity  kappa(nu) = sum_lines S Phi(nu)              Sec. 2.3 (kappa = S Phi)
- *   Voigt    Phi = sqrt(ln2/pi) H_V(a,u) / Gamma_D        Sec. 2.4
+ *   Voigt    Phi = sqrt(ln2/pi) H_V(a,u) / Gamma_D        Sec. 2.3
  *   H_V by Algorithm 916 for a^2+u^2 < 100, 3-node Gauss-Hermite for
- *   100 <= a^2+u^2 < 1e6 and 1-node Gauss-Hermite beyond  Sec. 2.5
- *   line-wing cutoff                                       Sec. 2.5
+ *   100 <= a^2+u^2 < 1e6 and 1-node Gauss-Hermite beyond  Sec. 2.4
+ *   line-wing cutoff                                       Sec. 2.4
  *   k-distribution: per-bin sort, k(g), Chebyshev fit      Sec. 2.2, 2.6
  *   transmission T(m) = int_0^1 exp(-k(g) m) dg            Sec. 2.1
  *
@@ -56,7 +56,7 @@ typedef struct {
     int64_t n;
 } helk_grid;
 
-/* Line-wing cutoff (Sec. 2.5).  A grid point i belongs to a line's window
+/* Line-wing cutoff (Sec. 2.4).  A grid point i belongs to a line's window
  * when |nu_i - nu0'| <= C, realised as the integer bounds
  *   i_lo = max(0, ceil((nu0' - C - nu_min)/dnu)),
  *   i_hi = min(n-1, floor((nu0' + C - nu_min)/dnu)).
@@ -98,7 +98,12 @@ typedef struct {
  *   HELK_PREC_F32_KAHAN: FP32 profile evaluation and Kahan-compensated FP32
  *                        accumulation, output converted to FP64.  Error vs the
  *                        FP64 form <= 1e-5 relative where kappa exceeds 1e-8
- *                        of its k-bin maximum. */
+ *                        of its k-bin maximum.  Needs every line's core
+ *                        (a^2 + u^2 < 100) within 2^23 grid points of its
+ *                        centre, i.e. a Doppler width below ~7e5 grid steps
+ *                        (point offsets are exact in FP32 only up to 2^24);
+ *                        otherwise the next helk_sync (or a call that reads
+ *                        results) returns HELK_ERR_UNSUPPORTED. */
 enum { HELK_PREC_F64 = 0, HELK_PREC_F32_KAHAN = 1 };
 
 typedef struct {
@@ -131,17 +136,19 @@ const char *helk_last_error(const helk_ctx *ctx);
 /* Change the stream later work is enqueued on. */
 helk_status helk_set_stream(helk_ctx *ctx, void *stream);
 
-/* Wait for all work of the context and report kernel-side errors (a bounded
- * wait that gave up: HELK_ERR_TIMEOUT, reported once; the context stays
- * usable). */
+/* Wait for all work of the context and report kernel-side errors, each
+ * once (the context stays usable): a bounded wait that gave up
+ * (HELK_ERR_TIMEOUT); an FP32-form call outside that form's range
+ * (HELK_ERR_UNSUPPORTED, see HELK_PREC_F32_KAHAN). */
 helk_status helk_sync(helk_ctx *ctx);
 
 /* Failure-detection self-test: launches a kernel whose bounded wait, the
  * one every staged copy of the Voigt kernels uses, waits on a barrier that
- * nothing completes; it gives up after `polls` polls (>= 1) and sets the
- * timeout flag, so the next helk_sync returns HELK_ERR_TIMEOUT.  No fault,
- * no hang. */
-helk_status helk_selftest_timeout(helk_ctx *ctx, int32_t polls);
+ * nothing completes.  The wait is bounded in time, by the GPU's global timer:
+ * it gives up after limit_us microseconds (1 .. 1e7; the Voigt kernels use
+ * 100 ms) and sets the timeout flag, so the next helk_sync returns
+ * HELK_ERR_TIMEOUT.  No fault, no hang. */
+helk_status helk_selftest_timeout(helk_ctx *ctx, int32_t limit_us);
 
 /* Upload (copy) a line list into context-owned device memory and order it
  * by nu0 (stable), replacing any previous list.  `on_device` = 0: the
@@ -151,7 +158,7 @@ helk_status helk_selftest_timeout(helk_ctx *ctx, int32_t polls);
 helk_status helk_lines_upload(helk_ctx *ctx, const helk_lines *lines,
                               int64_t n, int32_t on_device);
 
-/* Opacity of the uploaded lines at one condition (Sec. 2.3-2.5):
+/* Opacity of the uploaded lines at one condition (Sec. 2.3-2.4):
  *   kappa_out[i] (=|+=) weight * sum_lines S' H_V(a, u_i),
  *   S' = S sqrt(ln2/pi)/Gamma_D, u_i = sqrt(ln2)(nu_i - nu0')/Gamma_D.
  * kappa_out: device pointer to grid->n doubles, or NULL to use a buffer
@@ -163,7 +170,7 @@ helk_status helk_opacity(helk_ctx *ctx, double T, double P_atm,
                          double *kappa_out);
 
 /* Opacities of the uploaded lines at n_cond conditions (T[k], P_atm[k]) on
- * one grid, in one persistent launch (Sec. 2.3-2.5; the paper's many (T, P)
+ * one grid, in one persistent launch (Sec. 2.3-2.4; the paper's many (T, P)
  * points).  kappa_out: device pointer to n_cond * grid->n doubles, row k =
  * condition k (NULL: the context's buffer, read by helk_kdist with
  * kappa == NULL and n = n_cond * grid->n -- the k-tables of all conditions
@@ -209,7 +216,14 @@ helk_status helk_opacity_stats(helk_ctx *ctx, int64_t *n_evals,
  * The sorted values equal those of any correct ascending sort, bit for
  * bit.  kappa holds non-negative values, as helk_opacity writes them (the
  * sort orders the IEEE bit patterns); for negative or NaN values the tables
- * are unspecified (an infinite or NaN largest value gives that mean). */
+ * are unspecified (an infinite or NaN largest value gives that mean).
+ * Arithmetic: the pseudo-inverse of the Chebyshev design matrix is built
+ * once per (N_b, ncheb) in FP64 (Householder QR) and kept as FP32 (high, low)
+ * pairs; per point, ln max(k_j, kappa_floor) is a float-float logarithm
+ * (absolute error < 2e-12 for |ln k| < 70) and c = P L a double-float dot
+ * product (relative error ~2^-46 of sum |P_kj L_j|); the mean is an exact
+ * 128-bit integer sum, rounded once to FP64.  Coefficients agree with an
+ * FP64 least-squares fit to ~1e-12 of max |c|. */
 helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
                        int32_t nbins, int32_t ncheb, double kappa_floor,
                        double *coeffs, double *mean, int32_t out_on_host,
@@ -261,8 +275,8 @@ int64_t helk_launch_count(const helk_ctx *ctx);
 
 /* Stage timing (tracing).  With profiling on, the library records a CUDA
  * event pair on the context stream around each stage it launches:
- *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.5)
- *   HELK_STAGE_VOIGT     the Voigt/opacity kernel (Sec. 2.4-2.5)
+ *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.4)
+ *   HELK_STAGE_VOIGT     the Voigt/opacity kernel (Sec. 2.3-2.4)
  *   HELK_STAGE_KDIST     per-bin sort and Chebyshev fit (Sec. 2.6)
  *   HELK_STAGE_SETUP     one-time pseudo-inverse of the Chebyshev basis
  * helk_stage_times synchronises and writes, for each stage, the summed
@@ -277,7 +291,7 @@ helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
 /* ----------------------------------------------------------------------
  * Surrogate network for the Voigt function (an addition to the paper's
  * method: a 2 -> 64 -> 64 -> 64 -> 1 SiLU network, BF16 tensor-core MMAs with
- * FP32 accumulation, that stands in for Algorithm 916 (Sec. 2.5, the region
+ * FP32 accumulation, that stands in for Algorithm 916 (Sec. 2.4, the region
  * a^2 + u^2 < 100) as K(x, y) = K_ref(x, y) exp(net(f1, f2)),
  *   K_ref = e^{-x^2} erfcx(y) + (1 - e^{-x^2}) y / (sqrt(pi)(x^2 + y^2)),
  *   f1 = 2 asinh|x| / asinh(10) - 1,  f2 = 2 (log10 y + 4) / 5 - 1,
@@ -326,6 +340,23 @@ helk_status helk_surrogate_validate(helk_ctx *ctx, int32_t nx, int32_t ny,
                                     int32_t per_cell, double tol,
                                     uint8_t *mask_host, double *err_host);
 
+/* Throughput probe of one arithmetic unit (no counterpart in the paper: the
+ * measured peaks the roofline fractions of the Voigt kernels are taken
+ * against).  kind:
+ *   HELK_PROBE_FFMA      FP32 fused multiply-add (the FP32 form's pipe)
+ *   HELK_PROBE_DFMA      FP64 fused multiply-add (the FP64 form's pipe)
+ *   HELK_PROBE_MUFU_RCP  MUFU reciprocal (rcp.approx; GH1/GH3 of the FP32 form)
+ *   HELK_PROBE_MUFU_EX2  MUFU base-2 exponential (ex2.approx)
+ * Fills every SM with independent dependency chains of that instruction,
+ * calibrates the loop to ~20 ms a launch, then times three launches with
+ * CUDA events on the context stream.  *ops_per_s: flops per second for the
+ * FMA kinds (an FMA counts 2), results per second for the MUFU kinds;
+ * *ms_per_launch (optional): the mean launch time.  Synchronises; uses the
+ * context's scratch buffer. */
+enum { HELK_PROBE_FFMA = 0, HELK_PROBE_DFMA = 1, HELK_PROBE_MUFU_RCP = 2, HELK_PROBE_MUFU_EX2 = 3 };
+helk_status helk_peak_probe(helk_ctx *ctx, int32_t kind, double *ops_per_s,
+                            double *ms_per_launch);
+
 /* Transmission of every bin for nm column masses m (Sec. 2.1, Eq. for T:
  * T(m) = int_0^1 exp(-k(g) m) dg; the paper's "Transmission" stage).
  *   sorted (device, nbins*nb doubles, e.g. kg_out of helk_kdist) or NULL:
@@ -341,28 +372,32 @@ helk_status helk_transmission(helk_ctx *ctx, int32_t nbins, int64_t nb,
                               int32_t ncheb, int32_t ng, int32_t nm,
                               const double *m, double *direct, double *fit);
 
-/* Allocation-free k-distribution tables (no counterpart in the paper; an
- * interface addition).  Same computation and outputs as helk_kdist with
- * device-pointer outputs, for callers that must not allocate device memory:
- * code that runs while a CUDA graph is being captured (cudaMalloc/cudaFree
- * are not stream-ordered and break or invalidate the capture), code inside a
- * framework whose pool allocator owns all device memory, and latency-bound
- * loops that cannot afford the device-wide synchronisation of cudaFree.
+/* Allocation-free k-distribution tables.  The paper has no counterpart: this
+ * is an interface addition.  Same computation and outputs as helk_kdist with
+ * device-pointer outputs, for callers that cannot call cudaMalloc: code that
+ * runs inside a framework whose caching allocator owns the device memory
+ * (a cudaMalloc beside it may fail once the pool has taken the memory, and
+ * cudaFree synchronises the whole device, stalling the framework's other
+ * streams), and host programs that allow no allocation once their set-up is
+ * done (fixed-budget or real-time loops).  The caller still allocates the
+ * inputs and outputs.
  *
  * It needs no context and calls no cudaMalloc, cudaFree or allocating
- * library routine.  Its scratch (the pseudo-inverse of the Chebyshev basis
- * and its QR work array) lives in a fixed 6 MiB device array that every GPU
- * loading the library holds until the process exits.  Limits: N_b = n/nbins
- * <= 12288 points per bin and 1 <= ncheb <= 32 (the bin sort then runs in
- * shared memory); larger requests return HELK_ERR_INVALID_ARG, as do null
+ * library routine.  Its scratch (the pseudo-inverse of the Chebyshev basis,
+ * its QR work array, the logarithm's table and the sizes they were built for)
+ * lives in a fixed 6 MiB device array that every GPU loading the library
+ * holds until the process exits.  Limits: N_b = n/nbins <= 12288 points per
+ * bin and 1 <= ncheb <= 32 (the bin sort then runs in shared memory); larger
+ * requests return HELK_ERR_INVALID_ARG before any GPU work, as do null
  * kappa/coeffs, n % nbins != 0 and kappa_floor <= 0.  Runs on the current
  * CUDA device and on `stream` (a cudaStream_t, NULL = legacy default).
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array, which keeps the last call's contents: the
- * pseudo-inverse for the last (N_b, ncheb) is reused when the next call on
- * that device has the same sizes and recomputed otherwise; no part of it
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array,
+ * which keeps the last call's contents: each call launches a set-up kernel
+ * that rebuilds the pseudo-inverse when the sizes recorded in the array
+ * differ from its own and returns at once otherwise, so nothing in the array
  * needs to start at zero.  Calls whose work overlaps on the GPU (other
  * streams, other host threads) race on the array: order them on one stream
  * or synchronise between them.

@@ -91,23 +91,23 @@ def _f64(a):
 
 # ---------------------------------------------------------------- Voigt ----
 def K916(x, y):
-    """Algorithm 916 core, Re w(x+iy) (Sec. 2.5)."""
+    """Algorithm 916 core, Re w(x+iy) (Sec. 2.4)."""
     return lib().or_K916(float(x), float(y))
 
 
 def gh3(x, y):
-    """3-node Gauss-Hermite Voigt (Sec. 2.5)."""
+    """3-node Gauss-Hermite Voigt (Sec. 2.4)."""
     return lib().or_gh3(float(x), float(y))
 
 
 def gh1(x, y):
-    """1-node Gauss-Hermite Voigt = Lorentz far wing (Sec. 2.5)."""
+    """1-node Gauss-Hermite Voigt = Lorentz far wing (Sec. 2.4)."""
     return lib().or_gh1(float(x), float(y))
 
 
 def voigt_H(a, u):
     """Region-dispatched H_V(a, u); returns (H, region) with region 0 = 916,
-    1 = GH3, 2 = GH1 (Sec. 2.5)."""
+    1 = GH3, 2 = GH1 (Sec. 2.4)."""
     reg = ctypes.c_int(0)
     h = lib().or_voigt_H(float(a), float(u), ctypes.byref(reg))
     return h, reg.value
@@ -118,7 +118,7 @@ class Condition:
     """One (T, P) condition with its grid and cutoff.
 
     T [K], P [atm], mass [amu], q_ratio = Q(T0)/Q(T) (used only when the line
-    list has lower-state energies), cutoff kind/value/cap as in Sec. 2.5,
+    list has lower-state energies), cutoff kind/value/cap as in Sec. 2.4,
     grid nu_i = nu_min + i*dnu for i < ngrid.
     """
 
@@ -145,7 +145,7 @@ def _line_ptrs(lines):
 
 
 def lineprep(lines, cond):
-    """Per-line records at one condition (Sec. 2.3-2.5)."""
+    """Per-line records at one condition (Sec. 2.3-2.4)."""
     n, ptrs, keep = _line_ptrs(lines)
     out = {k: np.empty(n) for k in ("nu0p", "S", "Sp", "ku", "a", "gD", "gL")}
     out["ilo"] = np.empty(n, dtype=np.int64)

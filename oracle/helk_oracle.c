@@ -16,9 +16,9 @@
  * (closed forms, mpmath, numpy/scipy library routines, brute force).
  *
  * Readings of the paper taken here (where it is silent or garbled):
- *  - Sec. 2.4 Voigt profile: the integrand is exp(-u'^2) (the printed sign is
+ *  - Sec. 2.3 Voigt profile: the integrand is exp(-u'^2) (the printed sign is
  *    lost); Gamma_D uses the shifted line centre.
- *  - Sec. 2.5: region thresholds are inclusive on the cheaper method:
+ *  - Sec. 2.4: region thresholds are inclusive on the cheaper method:
  *    a^2+u^2 >= 100 -> 3-point Gauss-Hermite, >= 1e6 -> 1-point rule.
  *  - "Third-order Gauss-Hermite" = the 3-node rule (nodes 0, +-sqrt(3/2)).
  *  - Algorithm 916 is the series form of Re w(x+iy) derived in
@@ -49,7 +49,7 @@
 #define OR_SQRTPI    1.7724538509055160272982     /* sqrt(pi)          */
 #define OR_GH3_T     1.2247448713915890490986     /* sqrt(3/2)         */
 
-/* Region thresholds on r^2 = a^2 + u^2 (Sec. 2.5). */
+/* Region thresholds on r^2 = a^2 + u^2 (Sec. 2.4). */
 #define OR_R2_GH3    100.0
 #define OR_R2_GH1    1.0e6
 
@@ -57,13 +57,13 @@
 #define OR_A916_H     0.5
 #define OR_A916_NTERM 40
 
-/* Cutoff kinds (Sec. 2.5): absolute, multiple of Gamma_L capped, none. */
+/* Cutoff kinds (Sec. 2.4): absolute, multiple of Gamma_L capped, none. */
 #define OR_CUT_ABS     0
 #define OR_CUT_LORENTZ 1
 #define OR_CUT_NONE    2
 
 /* =====================================================================
- * Voigt function H_V(a,u) = Re w(u + i a)   (Sec. 2.4, Eq. for H_V)
+ * Voigt function H_V(a,u) = Re w(u + i a)   (Sec. 2.3, Eq. for H_V)
  * ===================================================================== */
 
 /* erfcx(y) = exp(y^2) erfc(y), from libm, for 0 <= y < 10 (the only range
@@ -71,7 +71,7 @@
 static double or_erfcx(double y) { return exp(y * y) * erfc(y); }
 
 /*
- * Algorithm 916 (Sec. 2.5): Re w(x + i y) for y >= 0 written with a scaled
+ * Algorithm 916 (Sec. 2.4): Re w(x + i y) for y >= 0 written with a scaled
  * complementary error function, cosines/sines and three exponentially
  * weighted series that share one loop.
  *
@@ -117,7 +117,7 @@ double or_K916(double x, double y)
 }
 
 /* Third-order (3-node) Gauss-Hermite quadrature of the Voigt integral
- * (Sec. 2.5): K ~ (y/pi) sum_k w_k / ((x - t_k)^2 + y^2), nodes 0 and
+ * (Sec. 2.4): K ~ (y/pi) sum_k w_k / ((x - t_k)^2 + y^2), nodes 0 and
  * +-sqrt(3/2), weights 2 sqrt(pi)/3 and sqrt(pi)/6. */
 double or_gh3(double x, double y)
 {
@@ -130,14 +130,14 @@ double or_gh3(double x, double y)
     return (y / OR_PI) * (w0 / d0 + w1 / d1 + w1 / d2);
 }
 
-/* First-order (1-node) Gauss-Hermite rule (Sec. 2.5): node 0, weight
+/* First-order (1-node) Gauss-Hermite rule (Sec. 2.4): node 0, weight
  * sqrt(pi), i.e. the Lorentz far-wing form y / (sqrt(pi) (x^2 + y^2)). */
 double or_gh1(double x, double y)
 {
     return (y / OR_PI) * (OR_SQRTPI / (x * x + y * y));
 }
 
-/* Region dispatch of Sec. 2.5 on r2 = u*u + a*a (each product and the sum
+/* Region dispatch of Sec. 2.4 on r2 = u*u + a*a (each product and the sum
  * rounded separately).  Returns which method ran in *region if non-NULL:
  * 0 = Algorithm 916, 1 = 3-point GH, 2 = 1-point GH. */
 double or_voigt_H(double a, double u, int *region)
@@ -150,7 +150,7 @@ double or_voigt_H(double a, double u, int *region)
 }
 
 /* =====================================================================
- * Line preparation (Sec. 2.3-2.5): per line and per (T, P) condition.
+ * Line preparation (Sec. 2.3-2.4): per line and per (T, P) condition.
  * ===================================================================== */
 
 typedef struct {
@@ -177,10 +177,10 @@ typedef struct {
  *    applied only when E'' is given; q_ratio = Q(T0)/Q(T) is an input.
  *  - Lorentz HWHM    Gamma_L = (T0/T)^n [a_air (P - Pself) + a_self Pself]/P0,
  *                    Pself = P/2, natural width dropped        (Sec. 2.3)
- *  - Doppler HWHM    Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c  (Sec. 2.4),
+ *  - Doppler HWHM    Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c  (Sec. 2.3),
  *                    m = the line's own mass when the list carries one
  *  - abundance       S is multiplied by the line's weight when given
- *  - cutoff C and window: inclusive |nu_i - nu0'| <= C        (Sec. 2.5)
+ *  - cutoff C and window: inclusive |nu_i - nu0'| <= C        (Sec. 2.4)
  */
 static void or_prep_one(const or_lines *L, int64_t l, double T, double P,
                         double mass, double q_ratio, int cut_kind,

@@ -5,7 +5,7 @@ and evaluates its own BF16 tensor-core version; this module is what its
 forward pass and its loss gradients are checked against.
 
 Network (2 -> 64 -> 64 -> 64 -> 1, SiLU): it stands in for the Voigt function
-K(x, y) = Re w(x + iy) where the method uses Algorithm 916 (Sec. 2.5:
+K(x, y) = Re w(x + iy) where the method uses Algorithm 916 (Sec. 2.4:
 x^2 + y^2 < 100), in the form
 
   K(x, y) = K_ref(x, y) * exp(net(f1, f2)),

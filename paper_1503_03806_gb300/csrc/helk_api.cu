@@ -184,10 +184,15 @@ helk_status helk_sync(helk_ctx *c) {
   HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "stream synchronize"));
   HELK_TRY(cuda_check(c, cudaMemcpy(c->stats_host, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost),
                       "read status"));
-  if (c->stats_host->err_flags & ERRF_TIMEOUT) {
+  const int flags = c->stats_host->err_flags;
+  if (flags) {
     // report once, then clear: the context stays usable
     HELK_TRY(cuda_check(c, cudaMemset(&c->stats->err_flags, 0, sizeof(int)), "clear status"));
-    return set_err(c, HELK_ERR_TIMEOUT, "a kernel's bounded wait gave up");
+    if (flags & ERRF_TIMEOUT) return set_err(c, HELK_ERR_TIMEOUT, "a kernel's bounded wait gave up");
+    if (flags & ERRF_F32_RANGE)
+      return set_err(c, HELK_ERR_UNSUPPORTED,
+                     "FP32 form: a line's core reaches beyond 2^23 grid points of its centre "
+                     "(Doppler width above ~7e5 grid steps); use the FP64 form");
   }
   return HELK_OK;
 }
@@ -952,11 +957,58 @@ helk_status helk_set_tile(helk_ctx *c, int32_t precision, int64_t n, int32_t til
   return HELK_OK;
 }
 
-helk_status helk_selftest_timeout(helk_ctx *c, int32_t polls) {
-  if (!c || polls < 1) return HELK_ERR_INVALID_ARG;
+helk_status helk_selftest_timeout(helk_ctx *c, int32_t limit_us) {
+  if (!c || limit_us < 1 || limit_us > 10 * 1000 * 1000) return HELK_ERR_INVALID_ARG;
   c->err.clear();
   HELK_TRY(bind_device(c));
-  return cuda_check(c, launch_selftest_timeout(c, polls), "selftest");
+  return cuda_check(c, launch_selftest_timeout(c, limit_us), "selftest");
+}
+
+helk_status helk_peak_probe(helk_ctx *c, int32_t kind, double *ops_per_s, double *ms_per_launch) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (kind < HELK_PROBE_FFMA || kind > HELK_PROBE_MUFU_EX2 || !ops_per_s)
+    return set_err(c, HELK_ERR_INVALID_ARG, "peak_probe: unknown kind or null output");
+  HELK_TRY(bind_device(c));
+  const int blocks = probe_blocks(c);
+  HELK_TRY(ensure_buf(c, &c->tmp, &c->tmp_cap, (int64_t)blocks * 8, "peak probe"));
+  cudaEvent_t e0, e1;
+  HELK_TRY(cuda_check(c, cudaEventCreate(&e0), "peak probe"));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_check(c, cudaErrorUnknown, "peak probe");
+  }
+  // calibrate the loop length to ~20 ms a launch, then time three launches
+  auto timed = [&](int iters, int reps, float *ms) -> helk_status {
+    helk_status st = cuda_check(c, cudaEventRecord(e0, c->stream), "peak probe");
+    for (int r = 0; r < reps && st == HELK_OK; ++r)
+      st = cuda_check(c, launch_probe(c, kind, iters, blocks, c->tmp), "peak probe");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventRecord(e1, c->stream), "peak probe");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventSynchronize(e1), "peak probe");
+    if (st == HELK_OK) st = cuda_check(c, cudaEventElapsedTime(ms, e0, e1), "peak probe");
+    return st;
+  };
+  float ms = 0.f;
+  int iters = 64;
+  helk_status st = timed(iters, 1, &ms);  // warm-up
+  for (int k = 0; k < 8 && st == HELK_OK && ms < 5.0f && iters < (1 << 22); ++k) {
+    iters *= 4;
+    st = timed(iters, 1, &ms);
+  }
+  if (st == HELK_OK && ms > 0.0f)
+    iters = (int)std::min<double>((double)(1 << 24), std::max(64.0, iters * 20.0 / ms));
+  const int reps = 3;
+  if (st == HELK_OK) st = timed(iters, reps, &ms);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HELK_TRY(st);
+  HELK_TRY(helk_sync(c));
+  const double per_launch = ms / reps;
+  const double ops = (double)blocks * probe_threads() * probe_ops_per_iter() * (double)iters *
+                     ((kind == HELK_PROBE_FFMA || kind == HELK_PROBE_DFMA) ? 2.0 : 1.0);
+  *ops_per_s = ops / (per_launch * 1e-3);
+  if (ms_per_launch) *ms_per_launch = per_launch;
+  return HELK_OK;
 }
 
 helk_status helk_set_profiling(helk_ctx *c, int32_t on) {

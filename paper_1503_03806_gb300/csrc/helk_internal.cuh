@@ -33,7 +33,7 @@ constexpr double SQRTPI = 1.7724538509055160272982;
 constexpr double INV_SQRTPI = 0.56418958354775628694808;
 constexpr double ASINH_XCORE = 2.99822295029796973884;  // asinh(10): the surrogate's |x| feature scale
 constexpr double GH3_T = 1.2247448713915890490986;       // sqrt(3/2)
-// Region thresholds on r^2 = a^2 + u^2 (Sec. 2.5)
+// Region thresholds on r^2 = a^2 + u^2 (Sec. 2.4)
 constexpr double R2_GH3 = 100.0;
 constexpr double R2_GH1 = 1.0e6;
 // Algorithm 916 series step and tail width: terms with |n h -+ x| > A916_TAIL
@@ -106,7 +106,11 @@ struct CondStats {
   int core_w1;                      // FP32 form: 1 + max distance (points) from a line's
                                     // reference index to a point of its core, 0: no core
 };
-enum { ERRF_TIMEOUT = 1 };
+// Kernel-side error flags (DevStats::err_flags), reported by helk_sync:
+//   ERRF_TIMEOUT    a bounded wait gave up
+//   ERRF_F32_RANGE  a line's core lies beyond 2^23 grid points of its centre,
+//                   where the FP32 form's point offsets are no longer exact
+enum { ERRF_TIMEOUT = 1, ERRF_F32_RANGE = 2 };
 
 // ---------------------------------------------------------- the context --
 }  // namespace helk
@@ -212,11 +216,24 @@ helk_status cuda_check(helk_ctx *c, cudaError_t e, const char *what);
 helk_status ensure_buf(helk_ctx *c, void **p, int64_t *cap_bytes, int64_t bytes,
                        const char *what);
 
-// Bounded wait on an mbarrier phase: returns false (and sets ERRF_TIMEOUT in
-// *flags) if the phase did not complete within `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_smem, uint32_t parity,
-                                                  int *flags, long long limit) {
-  for (long long it = 0; it < limit; ++it) {
+// Nanoseconds of the GPU's global timer (it keeps running while a kernel
+// waits or is preempted).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: polls mbarrier.try_wait (which may
+// suspend the thread for a while on each poll) until the phase completes or
+// `limit_ns` nanoseconds of the global timer have passed since the first
+// failed poll; then sets ERRF_TIMEOUT in *flags and returns false.  The bound
+// is in time, not in polls, so it holds whatever a poll's suspension costs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_smem, uint32_t parity, int *flags,
+                                                  unsigned long long limit_ns) {
+  bool started = false;
+  unsigned long long t0 = 0;
+  for (;;) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -226,9 +243,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_smem, uint32_t p
         : "r"(mbar_smem), "r"(parity)
         : "memory");
     if (done) return true;
+    const unsigned long long t = global_ns();
+    if (!started) {
+      started = true;
+      t0 = t;
+    } else if (t - t0 >= limit_ns) {
+      atomicOr(flags, ERRF_TIMEOUT);
+      return false;
+    }
   }
-  atomicOr(flags, ERRF_TIMEOUT);
-  return false;
 }
 
 // The lanes of the warp whose 8-bit digit equals this lane's (what a
@@ -315,7 +338,7 @@ int f64_shape_candidates(int *out, int max);
 int f64_shape(helk_ctx *c, int count, int64_t n);
 cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const helk_opts &o, double *kappa,
                              int shape, int64_t ntiles);
-cudaError_t launch_selftest_timeout(helk_ctx *c, int polls);
+cudaError_t launch_selftest_timeout(helk_ctx *c, int limit_us);
 // k_kdist.cu
 int64_t pinv_bytes(int64_t nb, int ncheb);
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
@@ -334,6 +357,12 @@ cudaError_t launch_mlp_samples(helk_ctx *c, int64_t n, uint64_t seed, float *fea
 cudaError_t launch_a916_points(helk_ctx *c, int64_t n, const double *x, const double *y, double *k);
 cudaError_t launch_mlp_validate(helk_ctx *c, int nx, int ny, int per_cell, double *err_dev);
 cudaError_t launch_mlp_queue(helk_ctx *c, int n_cond, int64_t ngrid, double weight, double *kappa);
+// k_probe.cu: throughput probes (kind: HELK_PROBE_*); sink holds `blocks`
+// doubles
+cudaError_t launch_probe(helk_ctx *c, int kind, int iters, int blocks, void *sink);
+int probe_blocks(helk_ctx *c);
+int probe_ops_per_iter();
+int probe_threads();
 cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double *sorted,
                                 const double *coef, int ncheb, int ng, int nm, const double *m_dev,
                                 double *direct, double *fit);

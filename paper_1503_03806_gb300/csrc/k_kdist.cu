@@ -130,12 +130,22 @@ __device__ double block_sum_pi(double v, double *red) {
   return s;
 }
 
+// `tag` (optional, device): the (N_b, n_cheb) whose pseudo-inverse P
+// already holds; the kernel returns at once when they equal this call's and
+// records them when it has rebuilt P.
 __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, double *work,
-                                                     double *vtv_out, double *P, float2 *lntab) {
+                                                     double *vtv_out, double *P, float2 *lntab,
+                                                     long long *tag) {
   __shared__ double red[PI_THREADS / 32];
   __shared__ double R[NCHEB_MAX * NCHEB_MAX];
   __shared__ double vtv[NCHEB_MAX];
+  __shared__ int s_current;
   const int tid = threadIdx.x;
+  if (tag) {
+    if (tid == 0) s_current = tag[0] == (long long)nb && tag[1] == (long long)ncheb;
+    __syncthreads();
+    if (s_current) return;
+  }
   // A, column-major
   for (int64_t j = tid; j < nb; j += PI_THREADS) {
     const double t = (double)(2 * j + 1) / (double)nb - 1.0;
@@ -231,6 +241,10 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
     lntab[tid] = make_float2(lh, (float)(l - (double)lh));
     lntab[128 + tid] = make_float2(ih, (float)(ic - (double)ih));
   }
+  if (tid == 0 && tag) {  // read by later launches only (stream order)
+    tag[0] = (long long)nb;
+    tag[1] = (long long)ncheb;
+  }
 }
 
 // The pseudo-inverse buffer: nb ncheb doubles of work space (the
@@ -243,7 +257,8 @@ static float2 *pinv_lntab(helk_ctx *c, int64_t nb, int ncheb) {
 
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
   ++c->launches;
-  k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv, pinv_lntab(c, nb, ncheb));
+  k_pinv<<<1, PI_THREADS, 0, c->stream>>>(nb, ncheb, work, nullptr, c->pinv, pinv_lntab(c, nb, ncheb),
+                                        nullptr);
   return cudaGetLastError();
 }
 
@@ -860,24 +875,21 @@ cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double
 // ------------------------------------------------ allocation-free variant --
 // Scratch of helk_kdist_static in a file-scope device array instead of
 // cudaMalloc'd memory: the pseudo-inverse of the Chebyshev basis (N_b x
-// n_cheb doubles) followed by the Householder work array of the same size
-// and the logarithm's table.
+// n_cheb doubles), the Householder work array of the same size, the
+// logarithm's table, and the (N_b, n_cheb) the pseudo-inverse was built for
+// (zero until the first build, so never equal to a valid pair).
 // Bins are limited to KDIST_STATIC_NB_MAX points (their sort then runs in
 // shared memory, so no other scratch is needed) and n_cheb to NCHEB_MAX:
 // 2 x 12288 x 32 x 8 B = 6 MiB, held by every device that loads the library
 // until the process exits.
 constexpr int64_t KDIST_STATIC_NB_MAX = 12288;
 constexpr int64_t KDIST_STATIC_PINV = KDIST_STATIC_NB_MAX * NCHEB_MAX;
-static __device__ __align__(256) double g_kdist_scratch[2 * KDIST_STATIC_PINV + KD_LNTAB];
+constexpr int64_t KDIST_STATIC_TAG = 2 * KDIST_STATIC_PINV + KD_LNTAB;  // offset of the size tag
+static __device__ __align__(256) double g_kdist_scratch[KDIST_STATIC_TAG + 2];
 
 namespace {
 constexpr int KDIST_STATIC_MAX_DEVICES = 64;
-struct StaticScratch {
-  double *ptr = nullptr;  // device address of g_kdist_scratch on this device
-  int64_t nb = 0;         // sizes whose pseudo-inverse the array holds
-  int ncheb = 0;
-};
-StaticScratch g_static[KDIST_STATIC_MAX_DEVICES];
+double *g_static_ptr[KDIST_STATIC_MAX_DEVICES];  // device address of g_kdist_scratch per device
 std::mutex g_static_mu;
 }  // namespace
 
@@ -907,29 +919,24 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
   double *ptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    StaticScratch &S = g_static[dev];
-    if (!S.ptr) {
+    if (!g_static_ptr[dev]) {
       // once per device, with that device current: the array's device address
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_kdist_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return HELK_ERR_CUDA;
       }
-      S.ptr = (double *)p;
+      g_static_ptr[dev] = (double *)p;
     }
-    ptr = S.ptr;
-    if (S.nb != nb || S.ncheb != ncheb) {
-      k_pinv<<<1, PI_THREADS, 0, st>>>(nb, ncheb, ptr + KDIST_STATIC_PINV, nullptr, ptr,
-                                       reinterpret_cast<float2 *>(ptr + 2 * KDIST_STATIC_PINV));
-      if (cudaGetLastError() != cudaSuccess) {
-        S.nb = 0;
-        S.ncheb = 0;
-        return HELK_ERR_CUDA;
-      }
-      S.nb = nb;
-      S.ncheb = ncheb;
-    }
+    ptr = g_static_ptr[dev];
   }
+  // The pseudo-inverse for these sizes: rebuilt on the device only when the
+  // sizes recorded in the array differ (the check runs in stream order, so
+  // it sees what earlier calls on the stream left there).
+  k_pinv<<<1, PI_THREADS, 0, st>>>(nb, ncheb, ptr + KDIST_STATIC_PINV, nullptr, ptr,
+                                   reinterpret_cast<float2 *>(ptr + 2 * KDIST_STATIC_PINV),
+                                   reinterpret_cast<long long *>(ptr + KDIST_STATIC_TAG));
+  if (cudaGetLastError() != cudaSuccess) return HELK_ERR_CUDA;
   if (cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -941,4 +948,3 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
                                                   nullptr, nullptr, coeffs, mean, kg_out);
   return cudaGetLastError() == cudaSuccess ? HELK_OK : HELK_ERR_CUDA;
 }
-

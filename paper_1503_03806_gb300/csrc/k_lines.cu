@@ -1,5 +1,5 @@
 // k_lines.cu -- line-list kernels: validation, ordering by nu0, per-condition
-// line preparation (Sec. 2.3-2.5) and the grid-tile -> line-range map.
+// line preparation (Sec. 2.3-2.4) and the grid-tile -> line-range map.
 //
 // This translation unit is compiled with --fmad=false: the quantities that
 // decide which grid points a line covers (window bounds) and which method
@@ -251,9 +251,9 @@ struct PrepArgs {
 //   S    = S0 (Q0/Q) e^{-c2E/T + c2E/T0} (1-e^{-c2 nu0/T})/(1-e^{-c2 nu0/T0})
 //   S   *= abundance weight of the line's species          (Sec. 2.1)
 //   Gamma_L = (T0/T)^n (g_air (P - P/2) + g_self P/2)      (Sec. 2.3)
-//   Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c               (Sec. 2.4)
+//   Gamma_D = nu0' sqrt(2 ln2 k_B T / m) / c               (Sec. 2.3)
 //   a = sqrt(ln2) Gamma_L / Gamma_D, ku = sqrt(ln2)/Gamma_D,
-//   S' = S sqrt(ln2/pi) / Gamma_D, window from the cutoff   (Sec. 2.5)
+//   S' = S sqrt(ln2/pi) / Gamma_D, window from the cutoff   (Sec. 2.4)
 // blockIdx.y is the condition; records of condition k start at k * n.
 __global__ void k_lineprep(int64_t n, const double *__restrict__ nu0, const double *__restrict__ S0,
                            const double *__restrict__ El, const double *__restrict__ gair,
@@ -407,7 +407,7 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // relative precision near the line centre.
 __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu, int64_t ngrid,
                          const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
-                         int2 *__restrict__ core_all, int32_t *__restrict__ ckey32) {
+                         int2 *__restrict__ core_all, int32_t *__restrict__ ckey32, int *err_flags) {
   const int cond = blockIdx.y;
   const LineRec64 *r64 = r64_all + (int64_t)cond * n;
   LineRec32 *r32 = r32_all + (int64_t)cond * n;
@@ -431,6 +431,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     // off the grid leaves its offset in phi, which has the sign of i - c, so
     // u = (i - c) beta - phi takes no cancellation)
     double cf = rint((r.nu0p - nu_min) * idnu);
+    const bool clamped = cf < 0.0 || cf > (double)(ngrid - 1);
     if (cf < 0.0) cf = 0.0;
     if (cf > (double)(ngrid - 1)) cf = (double)(ngrid - 1);
     q.c = (int32_t)cf;
@@ -458,18 +459,30 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     }
     r32[l] = q;
     // The line's core in the FP32 arithmetic of the Voigt kernels: points with
-    // fma(u, u, a^2) < 100, u = fma(i - c, beta, -phi), so |u| < 10 and
-    // |i - c| <= (10 + |phi|)/beta; the farthest such point from the
-    // reference index bounds the core kernel's candidate search.
+    // fma(u, u, a^2) < 100, u = fma(i - c, beta, -phi), so |u| < 10.  With the
+    // centre on the grid (|phi| <= beta/2) that needs |i - c| <= (10 + |phi|)/beta.
+    // With a centre off the grid, c clamped to the nearer end, phi has the
+    // sign of i - c, so |u| = |i - c| beta + |phi| and the core needs
+    // |i - c| < (10 - |phi|)/beta: none once |phi| >= 10.  The farthest core
+    // point from the reference index bounds the core kernel's candidate
+    // search.
     int2 core = make_int2(1, 0);
     if (q.a2 < 100.0f && q.ihi >= q.ilo && q.beta > 0.0f) {
-      // an upper bound (FP32 quotient, rounding covered by the margin of 2)
-      const double dmax = (double)ceilf((10.001f + fabsf(q.phi_k)) / q.beta) + 2.0;
-      const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
-      if (clo <= chi) {
-        const double w = fmax(key - clo, chi - key);
-        cw1 = max(cw1, (int)fmin(w + 1.0, 2.0e9));
-        core = make_int2((int)clo, (int)chi);
+      const float reach = clamped ? 10.001f - fabsf(q.phi_k) : 10.001f + fabsf(q.phi_k);
+      if (reach > 0.0f) {
+        // an upper bound (FP32 quotient, rounding covered by the margin of 2)
+        const double dmax = (double)ceilf(reach / q.beta) + 2.0;
+        // Both Voigt kernels take i - c exactly in FP32 only within 2^24
+        // points of c, so a core must end within 2^23 points (beta above
+        // ~1.2e-6: a Doppler width below ~7e5 grid steps); else the call is
+        // reported as unsupported by the FP32 form.
+        if (dmax >= 8388608.0) atomicOr(err_flags, ERRF_F32_RANGE);
+        const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
+        if (clo <= chi) {
+          const double w = fmax(key - clo, chi - key);
+          cw1 = max(cw1, (int)fmin(w + 1.0, 2.0e9));
+          core = make_int2((int)clo, (int)chi);
+        }
       }
     }
     core_all[(int64_t)cond * n + l] = core;
@@ -484,7 +497,7 @@ cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
   ++c->launches;
   k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, g.n, c->ckey, c->cstats, c->rec32,
-                                        c->core_rng, c->ckey32);
+                                        c->core_rng, c->ckey32, &c->stats->err_flags);
   return cudaGetLastError();
 }
 

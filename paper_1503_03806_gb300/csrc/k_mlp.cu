@@ -3,7 +3,7 @@
 // m16n8k16, FP32 accumulation).
 //
 // It stands in for K(x, y) = Re w(x + iy) where the method uses Algorithm 916
-// (Sec. 2.5: x^2 + y^2 < 100), as K = K_ref exp(net(f1, f2)) with
+// (Sec. 2.4: x^2 + y^2 < 100), as K = K_ref exp(net(f1, f2)) with
 //   K_ref = e^{-x^2} erfcx(y) + (1 - e^{-x^2}) y / (sqrt(pi)(x^2 + y^2)),
 //   f1 = 2 asinh|x| / asinh(10) - 1,  f2 = 2 (log10 y + 4) / 5 - 1,
 // so the network learns the residual ln(K / K_ref), |.| < 0.4.

@@ -1,5 +1,5 @@
 // k_voigt.cu -- the FP32 form of the line-tiled Voigt opacity kernel
-// (Sec. 2.3-2.5): FP32 profile evaluation on records with strengths scaled by
+// (Sec. 2.3-2.4): FP32 profile evaluation on records with strengths scaled by
 // 2^-E, Kahan-compensated FP32 accumulation per point, the result converted
 // to FP64 and rescaled at the flush; its Algorithm 916 cores in a separate
 // kernel that runs beside it on a second stream; the table of kernel shapes
@@ -213,7 +213,7 @@ __device__ void f32_issue(F32Pipe &P, LineRec32 (*sl)[LCH], unsigned long long s
 __device__ void f32_drain(F32Pipe &P, int *flags) {
   for (int s = 0; s < F32_STAGES; ++s) {
     const int pend = *((volatile int *)&P.pending[s]);
-    if (pend) mbar_wait_bounded(smem_addr(&P.full[s]), (uint32_t)(pend - 1), flags, WAIT_LIMIT);
+    if (pend) mbar_wait_bounded(smem_addr(&P.full[s]), (uint32_t)(pend - 1), flags, WAIT_LIMIT_NS);
   }
 }
 
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       }
       return;
     }
-    if (!mbar_wait_bounded(smem_addr(&P.full[s]), (seq / F32_STAGES) & 1u, &st->err_flags, WAIT_LIMIT)) {
+    if (!mbar_wait_bounded(smem_addr(&P.full[s]), (seq / F32_STAGES) & 1u, &st->err_flags, WAIT_LIMIT_NS)) {
       if (lane == 0) f32_drain(P, &st->err_flags);
       return;
     }

@@ -1,5 +1,5 @@
 // k_voigt64.cu -- the FP64 form of the line-tiled Voigt opacity kernel
-// (Sec. 2.3-2.5): FP64 throughout; u and r^2 use explicitly rounded
+// (Sec. 2.3-2.4): FP64 throughout; u and r^2 use explicitly rounded
 // operations so that the method chosen per point matches the FP64 definition
 // bit for bit.
 //
@@ -81,10 +81,10 @@ struct LineStager {
   __device__ bool acquire(int ch, int *flags) {
     if (threadIdx.x == 0 && ch + 1 < nch) issue(ch + 1);
     const uint32_t g = gbase + ch;
-    const bool ok = mbar_wait_bounded(mb[g & 1], (g >> 1) & 1, flags, WAIT_LIMIT);
+    const bool ok = mbar_wait_bounded(mb[g & 1], (g >> 1) & 1, flags, WAIT_LIMIT_NS);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0 && ch + 1 < nch)
-        mbar_wait_bounded(mb[(g + 1) & 1], ((g + 1) >> 1) & 1, flags, WAIT_LIMIT);
+        mbar_wait_bounded(mb[(g + 1) & 1], ((g + 1) >> 1) & 1, flags, WAIT_LIMIT_NS);
       return false;
     }
     return true;
@@ -201,20 +201,20 @@ __global__ void __launch_bounds__(BLOCK)
 
 // ------------------------------------------------- failure-detection test --
 // One thread waits, with the same bounded wait as the Voigt kernels, on an
-// mbarrier phase that nothing completes; after `polls` polls it sets the
-// timeout flag and returns.
-__global__ void k_selftest_timeout(DevStats *st, long long polls) {
+// mbarrier phase that nothing completes; after `limit_ns` nanoseconds of the
+// global timer it sets the timeout flag and returns.
+__global__ void k_selftest_timeout(DevStats *st, unsigned long long limit_ns) {
   __shared__ __align__(8) unsigned long long mbar;
   if (threadIdx.x != 0) return;
   const uint32_t mb = smem_addr(&mbar);
   mbar_init(mb, 1);
   fence_mbar_init();
-  mbar_wait_bounded(mb, 0, &st->err_flags, polls);
+  mbar_wait_bounded(mb, 0, &st->err_flags, limit_ns);
 }
 
-cudaError_t launch_selftest_timeout(helk_ctx *c, int polls) {
+cudaError_t launch_selftest_timeout(helk_ctx *c, int limit_us) {
   ++c->launches;
-  k_selftest_timeout<<<1, 32, 0, c->stream>>>(c->stats, polls);
+  k_selftest_timeout<<<1, 32, 0, c->stream>>>(c->stats, (unsigned long long)limit_us * 1000ull);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 // voigt_common.cuh -- pieces shared by the Voigt kernel files and the tile
-// map: the bounded-wait limit of the bulk-copy barriers, the occupancy
+// map: the time limit of the bulk-copy barrier waits, the occupancy
 // helpers of the persistent launches, and a warp-cooperative search of the
 // lines' sorted reference indices.
 #pragma once
@@ -12,7 +12,10 @@
 
 namespace helk {
 
-constexpr long long WAIT_LIMIT = 1ll << 24;  // polls of a bulk-copy barrier
+// Time limit of a bulk-copy barrier wait: a chunk's copy and the slowest
+// warp's work on the chunks before it take microseconds, so 100 ms is only
+// reached when something is wrong.
+constexpr unsigned long long WAIT_LIMIT_NS = 100ull * 1000 * 1000;
 
 template <typename K>
 static int resident_ctas(helk_ctx *c, K kern, int block) {

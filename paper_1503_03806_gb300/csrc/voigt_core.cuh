@@ -10,7 +10,7 @@
 namespace helk {
 
 // ------------------------------------------------------------------------
-// Algorithm 916 (Sec. 2.5), FP64.  K(x, y) for 0 <= x, x^2 + y^2 < 100:
+// Algorithm 916 (Sec. 2.4), FP64.  K(x, y) for 0 <= x, x^2 + y^2 < 100:
 //   K = e^{-x^2} erfcx(y) cos(2xy) + (2hx/pi) e^{-x^2} sin(xy) sinc(xy)
 //     + (2h/pi) [ -y cos(2xy) e^{-x^2} S1 + (y/2)(S2 + S3) ],
 //   S1 = sum e^{-(nh)^2}/((nh)^2+y^2)  (per line: sig1),

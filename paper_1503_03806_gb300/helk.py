@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "HELK_OK", -1: "HELK_ERR_INVALID_ARG", -2: "HELK_ERR_OOM", -3
                 -4: "HELK_ERR_STATE", -5: "HELK_ERR_TIMEOUT", -6: "HELK_ERR_UNSUPPORTED"}
 
 HELK_CUT_ABS, HELK_CUT_LORENTZ, HELK_CUT_NONE = 0, 1, 2
+HELK_PROBE_FFMA, HELK_PROBE_DFMA, HELK_PROBE_MUFU_RCP, HELK_PROBE_MUFU_EX2 = 0, 1, 2, 3
 HELK_PREC_F64, HELK_PREC_F32_KAHAN = 0, 1
 
 
@@ -88,6 +89,7 @@ SIGNATURES = [
     ("helk_tile_shape", ctypes.c_int, [_I32, _I32, _P, _P, _P]),
     ("helk_launch_count", _I64, [_P]),
     ("helk_set_tile", ctypes.c_int, [_P, _I32, _I64, _I32]),
+    ("helk_peak_probe", ctypes.c_int, [_P, _I32, _P, _P]),
 ]
 HELK_NSTAGES = 4
 MLP_NPARAMS = 8577
@@ -403,6 +405,13 @@ class Context:
         _check(self.h, lib.helk_surrogate_validate(self.h, nx, ny, per_cell, float(tol),
                                                    mask.ctypes.data_as(_P), err.ctypes.data_as(_P)))
         return mask.reshape(ny, nx), err.reshape(ny, nx)
+
+    def peak_probe(self, kind):
+        """Measured throughput of one arithmetic unit (HELK_PROBE_*):
+        (ops per second, ms per launch)."""
+        ops, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(self.h, lib.helk_peak_probe(self.h, int(kind), ctypes.byref(ops), ctypes.byref(ms)))
+        return ops.value, ms.value
 
     def set_profiling(self, on):
         helk_set_profiling(self.h, on)

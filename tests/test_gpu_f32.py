@@ -147,3 +147,24 @@ def test_launch_count_of_one_call(ctx):
         n0 = ctx.launch_count()
         case.gpu(ctx, precision=prec)
         assert ctx.launch_count() - n0 == expect, prec
+
+
+@pytest.mark.parametrize("cut", [("abs", 5.0), ("none",)])
+def test_lines_just_outside_the_grid(ctx, cut):
+    # Doppler cores ~0.8 cm^-1 wide on a 0.001 cm^-1 grid: lines centred just
+    # outside the grid (their reference index clamped to the nearer end) whose
+    # cores reach onto it, lines farther out whose cores do not, and lines
+    # inside; the cores of the clamped lines must be found by the core kernel
+    # and skipped by the main kernel exactly as on the grid
+    rng = np.random.default_rng(404)
+    nu = np.sort(np.concatenate([rng.uniform(19998.0, 20000.0, 20), rng.uniform(20000.0, 20010.0, 60),
+                                 rng.uniform(20010.0, 20012.0, 20)]))
+    lines = {"nu0": nu, "S0": 10.0 ** rng.uniform(-24, -20, nu.size), "gamma_air": rng.uniform(0.02, 0.1, nu.size)}
+    case = Case(1500.0, 0.01, 18.0, (20000.0, 0.001, 10000), cut)
+    ctx.upload(lines)
+    k = f32(ctx, case, count_regions=True)
+    ko, evo, rego = oracle.opacity(lines, case.oracle_cond(), nthreads=NTHREADS)
+    ev, reg = ctx.stats(with_regions=True)
+    assert ev == evo and rego[0] > 0
+    assert np.abs(reg[:3] - rego).sum() <= max(4, 1e-4 * evo)
+    check_binned(k, ko, 10, "lines just outside the grid, %s" % cut[0])

@@ -1,4 +1,4 @@
-"""GPU parity of the opacity stage (Sec. 2.3-2.5): the CUDA path through the
+"""GPU parity of the opacity stage (Sec. 2.3-2.4): the CUDA path through the
 C ABI against the FP64 oracle on the same seeded inputs.
 
 FP64 form: 1e-9 relative per grid point (every term is computed from the

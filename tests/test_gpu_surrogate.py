@@ -25,7 +25,7 @@ import pytest
 import oracle
 from oracle import mlp
 from paper_1503_03806_gb300 import synth
-from tests.helpers import NTHREADS, Case
+from tests.helpers import NTHREADS, Case, check_sampled_f32, near_lines
 
 pytestmark = pytest.mark.gpu
 
@@ -161,17 +161,17 @@ def test_full_size_surrogate_workload(ctx, trained):
     case = Case(w["T"][0], w["P_atm"][0], w["mass"], grid, w["cut"], q_ratio=(296.0 / w["T"][0]) ** 1.5)
     ctx.upload(lines)
     k = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN, surrogate=True).cpu().numpy()
-    nb = w["ngrid"] // w["nbins"]
-    bmax = k.reshape(w["nbins"], nb).max(axis=1)
     rng = np.random.default_rng(12)
     reach = w["cut"][2] + grid[1]
+    cond = case.oracle_cond()
+
+    def oracle_at(pts):
+        near = near_lines(lines, grid[0] + pts[0] * grid[1], grid[0] + pts[-1] * grid[1], reach)
+        return oracle.opacity_points(near, cond, pts)[0]
+
+    # thresholds from the oracle, with each touched bin's device maximum
+    # checked as well (tests/helpers.py: check_sampled_f32)
     for lo in (2000.0, 15000.0, 28000.0):
         i0 = int((lo - grid[0]) / grid[1])
         idx = np.sort(rng.choice(np.arange(i0, i0 + 20_000), 60, replace=False))
-        a, b = np.searchsorted(lines["nu0"], [grid[0] + idx[0] * grid[1] - reach,
-                                              grid[0] + idx[-1] * grid[1] + reach])
-        near = {kk: np.ascontiguousarray(v[a:b]) for kk, v in lines.items()}
-        ko, _ = oracle.opacity_points(near, case.oracle_cond(), idx)
-        sel = k[idx] > 1e-8 * bmax[idx // nb]
-        assert sel.sum() > 0
-        assert np.max(np.abs(k[idx][sel] / ko[sel] - 1)) < 1e-4, lo
+        check_sampled_f32(k, w["nbins"], idx, oracle_at, 1e-4, 1e-8, "surrogate workload at %g" % lo)

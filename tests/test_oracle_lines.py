@@ -1,5 +1,5 @@
 """Pins of the oracle's line preparation and opacity accumulation
-(Sec. 2.3-2.5): hand values, brute-force windows and counts, profile
+(Sec. 2.3-2.4): hand values, brute-force windows and counts, profile
 normalisation, linearity, thread independence."""
 import math
 
@@ -33,7 +33,7 @@ def test_doppler_width_hand_value():
                                rtol=2e-6)
     # Gamma_L = gamma P (T0/T)^0.5 with gamma_self = gamma_air (Sec. 2.3)
     np.testing.assert_allclose(r["gL"], 0.05 * math.sqrt(296.0 / 1500.0), rtol=1e-15)
-    # damping and scale parameters (Sec. 2.4)
+    # damping and scale parameters (Sec. 2.3)
     np.testing.assert_allclose(r["a"], math.sqrt(math.log(2)) * r["gL"] / r["gD"], rtol=1e-15)
     np.testing.assert_allclose(r["Sp"], 1e-20 * math.sqrt(math.log(2) / math.pi) / r["gD"],
                                rtol=1e-15)
@@ -118,7 +118,7 @@ def test_single_line_equals_Sp_times_H():
 
 
 def test_profile_is_normalised():
-    # sum_i Phi(nu_i) dnu = 1 (Sec. 2.4) on a fine grid without cutoff, with the
+    # sum_i Phi(nu_i) dnu = 1 (Sec. 2.3) on a fine grid without cutoff, with the
     # Lorentzian tails beyond the grid added analytically.
     S = 1.0
     lines = {"nu0": np.array([1000.0]), "S0": np.array([S]), "gamma_air": np.array([0.02])}

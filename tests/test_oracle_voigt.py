@@ -1,4 +1,4 @@
-"""Pins of the oracle's Voigt function (Sec. 2.4-2.5) against references that
+"""Pins of the oracle's Voigt function (Sec. 2.3-2.4) against references that
 do not reuse its formulas: mpmath's w(z), scipy's erfcx, numpy's
 Gauss-Hermite nodes, scipy quadrature of the convolution integral."""
 import math
@@ -35,7 +35,7 @@ def _core_points(n, seed):
 
 
 def test_k916_matches_mpmath_over_core_region():
-    # Algorithm 916 (Sec. 2.5) is accurate to ~1e-15; the oracle's erfcx
+    # Algorithm 916 (Sec. 2.4) is accurate to ~1e-15; the oracle's erfcx
     # (exp(y^2) erfc(y)) costs up to ~1e-14 near y = 10.
     worst = 0.0
     for x, y in _core_points(1500, 1):

@@ -1,13 +1,15 @@
 """The allocation-free k-distribution entry point, helk_kdist_static, called
 through the C ABI, against the regular entry point helk_kdist.
 
-helk_kdist_static exists for callers that must not allocate device memory
-(for example code running under CUDA graph capture, or inside a framework
-whose pool allocator owns all device memory): its scratch is a fixed device
-array inside the library.  Its outputs must equal those of helk_kdist within
-the k-distribution tests' tolerances (sorted values bit for bit, coefficients
-to 1e-9 of max|c|, bin means to 1e-12), on consecutive calls that reuse and
-then replace the scratch contents.  This file is collected last on purpose.
+helk_kdist_static serves callers that cannot allocate device memory, such as
+code inside a framework whose caching allocator owns the device memory, or a
+host program that allows no allocation once its set-up is done: its scratch
+is a fixed device array inside the library.  Its outputs must equal those of
+helk_kdist within the k-distribution tests' tolerances (sorted values bit for
+bit, coefficients to 1e-9 of max|c|, bin means to 1e-12), on consecutive calls
+that reuse the scratch, replace its contents with other sizes, and then go
+back to the first sizes.  This file is collected last on purpose: it passes
+alone in a fresh process and after every other test.
 """
 import ctypes
 
@@ -41,9 +43,11 @@ def test_static_entry_point_matches_regular():
     stream = torch.cuda.current_stream().cuda_stream
     ctx = helk.Context(0)
     try:
-        # two calls with the same sizes (the second reuses the scratch), then
-        # one with new sizes (the scratch is rewritten)
-        for nbins, nb, ncheb, seed in [(30, 10000, 20, 1), (30, 10000, 20, 2), (7, 12288, 32, 3)]:
+        # two calls in a row with the same sizes (the second reuses the
+        # scratch), one with new sizes (the scratch is rebuilt), then the
+        # first sizes again (rebuilt once more)
+        for nbins, nb, ncheb, seed in [(30, 10000, 20, 1), (30, 10000, 20, 2), (7, 12288, 32, 3),
+                                       (30, 10000, 20, 4)]:
             k = torch.from_numpy(synth.uniform_kappa(nbins * nb, seed)).cuda()
             st, coef, mean, srt = _call_static(helk, k, nbins, ncheb, 1e-250, stream)
             torch.cuda.synchronize()
