@@ -62,7 +62,7 @@ def probe_peaks(ctx, helk, device_index):
             out[name.rsplit("_", 1)[0] + "_ms_per_launch"] = ms
     out["clocks"] = clk.summary()
     out["how"] = ("helk_peak_probe: every SM filled with 8 independent chains a thread of one instruction "
-                  "(FP32 FMA, FP64 FMA, rcp.approx, ex2.approx), loop calibrated to ~20 ms a launch, mean of "
+                  "(FP32 FMA, FP64 FMA, rcp.approx after an FP32 add, ex2.approx), loop calibrated to ~20 ms a launch, mean of "
                   "3 launches by CUDA events; FMA counted as 2 flops; burst figure (kernel timed alone)")
     return out
 
@@ -534,6 +534,26 @@ def run_ours(args):
                                                 "surrogate step without the L2 flush"}
         del km
 
+    # the paper's Transmission stage (Sec. 3.5: 1000 column masses per bin) on
+    # the medium workload's k-tables: from the sorted values and from the fit
+    trans = None
+    if not args.no_transmission:
+        trans = leg_transmission(ctx, w, T, P, mass, cut, grid, PREC["f32"])
+
+    # the 1e7-line workload at 1500 K, 1 atm: opacity + k-tables per (T, P),
+    # FP32 with and without the surrogate (when its leg trained one)
+    surrw = None
+    if not args.no_surrogate_workload:
+        surrw = leg_surrogate_workload(ctx, args, PREC["f32"], trained=surr is not None, flush=flush)
+        ctx.upload(lines)
+
+    # the mixed workload: 1e8 lines of 4 species, 16 conditions in one batch
+    # call, then the k-tables of all of them in one call
+    mixed = None
+    if not args.no_mixed:
+        mixed = leg_mixed(ctx, PREC["f32"], local_rank, peaks)
+        ctx.upload(lines)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -564,11 +584,162 @@ def run_ours(args):
                         "stages_ms_per_step": r64["stages"], "roofline": r64["roofline"],
                         "gpu_launches": r64["launches"]},
                "speedup_f32_vs_f64": r32["value"] / r64["value"],
-               "tp_grid": tpg, "surrogate": surr}
+               "tp_grid": tpg, "surrogate": surr, "surrogate_workload": surrw, "mixed": mixed,
+               "transmission": trans}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def leg_transmission(ctx, w, T, P, mass, cut, grid, prec):
+    """Transmission of every bin of the medium workload for 1000 column
+    masses (log-spaced), from the sorted k(g) and from the 20-coefficient fit
+    resampled on 1000 points: the paper's last stage, timed by CUDA events."""
+    import numpy as np
+    import torch
+    nbins, ncheb = w["nbins"], w["ncheb"]
+    kap = ctx.opacity(T, P, mass, cut, grid, precision=prec)
+    coef, _, srt = ctx.kdist(kap, nbins, ncheb, want_sorted=True)
+    m = np.logspace(14.0, 30.0, 1000)  # molecules cm^-2 (kappa is per molecule)
+    out = {}
+    for name, kw in (("direct", dict(sorted_k=srt)), ("fit", dict(coeffs=coef, ng=1000))):
+        ctx.transmission(nbins, m, **kw)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            ctx.transmission(nbins, m, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = a.elapsed_time(b) / 3
+    out["what"] = ("T_b(m) for %d bins x 1000 column masses: direct = midpoint rule over the %d sorted "
+                   "values of each bin (FP64 exp), fit = midpoint rule over 1000 points of the resampled "
+                   "k(g)" % (nbins, grid[2] // nbins))
+    return out
+
+
+def timed_steps(step, steps, warmup, flush):
+    """Mean device time of `steps` calls of step() after `warmup` untimed
+    ones, the L2 flushed before each (outside the events)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def leg_surrogate_workload(ctx, args, prec, trained, flush):
+    """The 1e7-line workload (log-normal strengths, lower-state energies) at
+    1500 K, 1 atm on the 3e6-point grid: opacity + 300 x 20 k-tables per
+    (T, P) in the FP32 form, and with the surrogate routed when a network was
+    trained and validated in this run."""
+    import torch
+    from paper_1503_03806_gb300 import synth
+    ws = synth.WORKLOADS["surrogate"]
+    ls = synth.workload_lines("surrogate")
+    g = (ws["nu_min"], ws["dnu"], ws["ngrid"])
+    Tq, Pq, q = ws["T"][0], ws["P_atm"][0], (296.0 / ws["T"][0]) ** 1.5
+    ctx.upload(ls)
+    del ls
+    k = torch.empty(g[2], dtype=torch.float64, device="cuda")
+    ctx.opacity(Tq, Pq, ws["mass"], ws["cut"], g, out=k, precision=prec, q_ratio=q, count_regions=True)
+    evals, reg = ctx.stats(with_regions=True)
+    out = {"workload": "surrogate: %d lines, %d-point grid, cutoff min(500 Gamma_L, 100 cm^-1), T %g K, "
+                       "P %g atm, %d bins x %d coefficients"
+                       % (ws["nlines"], g[2], Tq, Pq, ws["nbins"], ws["ncheb"]),
+           "evals_per_step": int(evals), "alg916_share": float(reg[0]) / max(1, int(evals))}
+    forms = {"fp32": False}
+    if trained:
+        forms["fp32_surrogate"] = True
+    for name, sur in forms.items():
+        def step():
+            ctx.opacity(Tq, Pq, ws["mass"], ws["cut"], g, out=k, precision=prec, q_ratio=q, surrogate=sur)
+            ctx.kdist(k, ws["nbins"], ws["ncheb"])
+        ms = timed_steps(step, max(3, min(args.steps, 10)), max(3, args.warmup), flush)
+        out[name] = {"ms_per_step": ms, "spectra_per_s": 1e3 / ms, "value": evals / (ms * 1e-3),
+                     "unit": UNIT}
+    if trained:
+        out["gain_vs_fp32"] = out["fp32"]["ms_per_step"] / out["fp32_surrogate"]["ms_per_step"]
+    del k
+    return out
+
+
+def leg_mixed(ctx, prec, device_index, peaks):
+    """The mixed workload: 1e8 lines of 4 species (per-line mass and
+    abundance weight), all 4 T x 4 P conditions in one helk_opacity_batch call
+    (FP32 form, records in chunks under the batch record budget) on the
+    3e7-point grid, then the k-tables of all 16 conditions (16000 bins of
+    30000 points, 20 coefficients) in one helk_kdist call.  One timed call of
+    each (a call is tens of seconds), clocks sampled."""
+    import numpy as np
+    import torch
+    from paper_1503_03806_gb300 import synth
+    wm = synth.WORKLOADS["mixed"]
+    parts = []
+    for sp, (m, x) in enumerate(zip(wm["species_mass"], wm["mixing"])):
+        L = synth.workload_lines("mixed", species=sp)
+        L["mass"] = np.full(L["nu0"].shape[0], m)
+        L["weight"] = np.full(L["nu0"].shape[0], x)
+        parts.append(L)
+    lm = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    del parts
+    order = np.argsort(lm["nu0"], kind="stable")
+    lm = {k: np.ascontiguousarray(v[order]) for k, v in lm.items()}
+    del order
+    g = (wm["nu_min"], wm["dnu"], wm["ngrid"])
+    Ts = np.repeat(np.asarray(wm["T"]), len(wm["P_atm"]))
+    Ps = np.tile(np.asarray(wm["P_atm"]), len(wm["T"]))
+    qs = (296.0 / Ts) ** 1.5
+    nc = len(Ts)
+    ctx.upload(lm)
+    nlines = lm["nu0"].shape[0]
+    del lm
+    kb = torch.empty((nc, g[2]), dtype=torch.float64, device="cuda")
+    with Clocks(device_index) as clk:
+        ctx.set_profiling(True)
+        a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        ctx.opacity_batch(Ts, Ps, 18.0, wm["cut"], g, out=kb, precision=prec, q_ratio=qs)
+        b.record()
+        ctx.kdist(kb.view(-1), nc * wm["nbins"], wm["ncheb"])
+        c2.record()
+        torch.cuda.synchronize()
+        st = ctx.stage_times()
+        ctx.set_profiling(False)
+    ev, _ = ctx.batch_stats(nc)
+    ms_op, ms_kd = a.elapsed_time(b), b.elapsed_time(c2)
+    total = ms_op + ms_kd
+    n_all = nc * g[2]
+    kd_gbs = 8.0 * n_all / (ms_kd * 1e-3) / 1e9
+    out = {"workload": "mixed: %d lines (4 species, masses %s amu, mixing 1/4), %d conditions (T %g-%g K x P "
+                       "%g-%g atm), %d-point grid at %g cm^-1, cutoff min(500 Gamma_L, 100 cm^-1), %d bins x %d "
+                       "coefficients per condition" % (nlines, wm["species_mass"], nc, min(Ts), max(Ts), min(Ps),
+                                                       max(Ps), g[2], g[1], wm["nbins"], wm["ncheb"]),
+           "form": "FP32 + Kahan, one helk_opacity_batch call (records in chunks under the 64 GiB budget) + "
+                   "one helk_kdist call",
+           "evals_per_call": int(ev.sum()), "evals_per_condition": [int(x) for x in ev],
+           "opacity_ms": ms_op, "kdist_ms": ms_kd, "ms_per_condition": total / nc,
+           "spectra_per_s": nc / (total * 1e-3), "value": float(ev.sum()) / (ms_op * 1e-3), "unit": UNIT,
+           "kdist_hbm": {"bytes": 8 * n_all, "achieved": kd_gbs, "unit": "GB/s",
+                         "peak": peaks.get("hbm_gbs"),
+                         "frac": kd_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                         "note": "bins of 30000 points: sorted through global ping-pong buffers"},
+           "stages_ms": {k: v[0] for k, v in st.items() if v[1]},
+           "clocks": clk.summary(), "timed_calls": 1}
+    del kb
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_profile_surrogate():
@@ -628,6 +799,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tp-grid", action="store_true", help="skip the batched 64-condition leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--no-surrogate-workload", action="store_true", help="skip the 1e7-line workload leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 1e8-line 16-condition leg")
+    ap.add_argument("--no-transmission", action="store_true", help="skip the transmission leg")
     ap.add_argument("--profile-case", choices=["f32", "f64", "surrogate"], default=None,
                     help="run a short fixed case for ncu and exit")
     args = ap.parse_args()

@@ -180,13 +180,25 @@ helk_status helk_opacity(helk_ctx *ctx, double T, double P_atm,
  * once per call shape (n_cond, line list, grid, cutoff, options, output
  * pointer, tile shape) into a CUDA graph and replayed on later calls with the
  * same shape; only the condition values change between replays.  The
- * results equal those of n_cond helk_opacity calls bit for bit.  A call
- * waits until the previous batch call has read its conditions. */
+ * per-condition line records take 64 B (FP64 form) or 120 B (FP32 form) per
+ * line; when those of all n_cond conditions exceed the record budget
+ * (64 GiB unless set by helk_set_batch_budget), the conditions run in the
+ * fewest equal chunks that fit, each chunk its own captured graph and
+ * persistent launch, one after the other on the stream (the context keeps
+ * the 16 most recent graphs).  The results equal those of n_cond
+ * helk_opacity calls bit for bit.  A call waits until the previous batch call
+ * has read its conditions. */
 helk_status helk_opacity_batch(helk_ctx *ctx, int32_t n_cond, const double *T,
                                const double *P_atm, const double *q_ratio,
                                double mass_amu, const helk_cutoff *cut,
                                const helk_grid *grid, const helk_opts *opts,
                                double *kappa_out);
+
+/* Line-record budget of one chunk of helk_opacity_batch, in bytes (0: the
+ * default, 64 GiB).  A chunk always holds at least one condition, so a
+ * budget below one condition's records runs the conditions one by one.
+ * Host-only. */
+helk_status helk_set_batch_budget(helk_ctx *ctx, int64_t bytes);
 
 /* Evaluation counts of the first n_cond conditions of the last opacity call
  * (n_evals[k]; region_counts[4k..4k+3] as in helk_opacity_stats when that call

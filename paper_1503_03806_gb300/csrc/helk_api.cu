@@ -158,7 +158,7 @@ void helk_destroy(helk_ctx *c) {
   if (c->cond_host) cudaFreeHost(c->cond_host);
   if (c->cstats_host) cudaFreeHost(c->cstats_host);
   if (c->cond_ev) cudaEventDestroy(c->cond_ev);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
@@ -524,6 +524,7 @@ helk_status helk_autotune(helk_ctx *c, double T, double P, double mass, const he
 }
 
 // ---------------------------------------------------------------- batch --
+
 // Many (T, P) conditions in one persistent Voigt launch; the whole sequence
 // (condition upload from pinned staging, statistics reset, line preparation,
 // FP32 records, tile maps, condition order, Voigt kernel) is captured once
@@ -536,7 +537,51 @@ static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const h
            g->dnu, (long long)g->n, o.precision, o.accumulate, o.weight, o.count_regions, o.surrogate,
            (const void *)kappa, shape, (const void *)c->rec64, (const void *)c->rec32,
            (const void *)c->tile_lo, (const void *)c->cstats, (const void *)c->squeue, (const void *)c->kcore);
-  return std::string(b);
+  // the line fields present (absent ones are passed to line preparation as
+  // null pointers) and the per-condition arrays of the chunk
+  char b2[192];
+  snprintf(b2, sizeof b2, "|%d%d%d%d%d%d|%p|%p|%p|%p", c->has_E, c->has_gself, c->has_ncoll, c->has_delta,
+           c->has_mass, c->has_weight, (const void *)c->cond_host, (const void *)c->cond_dev,
+           (const void *)c->cond_order, (const void *)c->core_rng);
+  return std::string(b) + b2;
+}
+
+// The per-condition arrays as seen by a chunk of a batch: offset by the
+// chunk's first condition for the lifetime of the view.
+struct CondView {
+  helk_ctx *c;
+  int k0;
+  CondView(helk_ctx *ctx, int first) : c(ctx), k0(first) {
+    c->cond_host += k0;
+    c->cond_dev += k0;
+    c->cstats += k0;
+    c->cond_order += k0;
+  }
+  ~CondView() {
+    c->cond_host -= k0;
+    c->cond_dev -= k0;
+    c->cstats -= k0;
+    c->cond_order -= k0;
+  }
+  CondView(const CondView &) = delete;
+  CondView &operator=(const CondView &) = delete;
+};
+
+static cudaGraphExec_t find_graph(helk_ctx *c, const std::string &key) {
+  for (auto &kv : c->graphs)
+    if (kv.first == key) return kv.second;
+  return nullptr;
+}
+
+// Keeps the last MAX_GRAPHS captured graphs (a graph still running when it
+// is dropped is freed when it completes).
+static void keep_graph(helk_ctx *c, const std::string &key, cudaGraphExec_t gx) {
+  constexpr size_t MAX_GRAPHS = 16;
+  if (c->graphs.size() >= MAX_GRAPHS) {
+    cudaGraphExecDestroy(c->graphs.front().second);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.emplace_back(key, gx);
 }
 
 helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, const double *P,
@@ -572,51 +617,77 @@ helk_status helk_opacity_batch(helk_ctx *c, int32_t n_cond, const double *T, con
   const int tile = shape_points(o.precision, shape);
   if (tile <= 0) return set_err(c, HELK_ERR_STATE, "opacity: no kernel shape");
   const int64_t ntiles = (g->n + tile - 1) / tile;
-  HELK_TRY(ensure_call_buffers(c, n_cond, o, ntiles, g->n));
+  // Conditions run in the fewest equal chunks whose line records fit the
+  // record budget (one chunk unless the list is very long), each chunk one
+  // captured graph; the chunks share the record, tile-map and core buffers
+  // and follow each other on the stream.
+  const int64_t rec_line =
+      (int64_t)sizeof(LineRec64) +
+      (o.precision == HELK_PREC_F32_KAHAN ? (int64_t)(sizeof(LineRec32) + sizeof(int2)) : 0);
+  const int64_t per_cond = std::max<int64_t>(c->nlines, 1) * rec_line;
+  const int gmax = (int)std::max<int64_t>(1, std::min<int64_t>(n_cond, c->batch_budget / per_cond));
+  const int nchunk = (n_cond + gmax - 1) / gmax;
+  const int chunk = (n_cond + nchunk - 1) / nchunk;
+  HELK_TRY(ensure_conds(c, n_cond));
+  HELK_TRY(ensure_call_buffers(c, chunk, o, ntiles, g->n));
   if (!c->cap_stream)
     HELK_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "graph stream"));
   if (!c->cond_ev) HELK_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->cond_ev, cudaEventDisableTiming), "graph"));
   // the previous batch must have read the staging buffer before it changes
   HELK_TRY(cuda_check(c, cudaEventSynchronize(c->cond_ev), "opacity_batch"));
   for (int k = 0; k < n_cond; ++k) c->cond_host[k] = CondArgs{T[k], P[k], q_ratio ? q_ratio[k] : o.q_ratio, 0.0};
-  const std::string key = batch_key(c, n_cond, mass, cut, g, o, kappa, shape);
-  if (!c->gexec || c->gkey != key) {
-    if (c->gexec) {
-      cudaGraphExecDestroy(c->gexec);
-      c->gexec = nullptr;
-    }
-    cudaStream_t user = c->stream;
-    c->stream = c->cap_stream;
-    cudaGraph_t graph = nullptr;
-    helk_status st = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal),
-                                "graph capture");
-    if (st == HELK_OK) {
-      st = cuda_check(c, cudaMemcpyAsync(c->cond_dev, c->cond_host, n_cond * sizeof(CondArgs),
-                                         cudaMemcpyHostToDevice, c->stream),
-                      "graph capture");
-      if (st == HELK_OK) st = prepare_lines(c, n_cond, nullptr, mass, cut, g, o);
-      if (st == HELK_OK) st = run_voigt(c, n_cond, g, o, kappa, shape, tile, ntiles);
-      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-      if (st == HELK_OK) st = cuda_check(c, e, "graph capture");
-    }
-    c->stream = user;
-    if (st == HELK_OK) st = cuda_check(c, cudaGraphInstantiate(&c->gexec, graph, 0), "graph instantiate");
-    if (graph) cudaGraphDestroy(graph);
-    if (st != HELK_OK) {
-      cudaGetLastError();
-      c->gexec = nullptr;
-      return st;
-    }
-    c->gkey = key;
-  }
   stage_begin(c, HELK_STAGE_VOIGT);
-  HELK_TRY(cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"));
+  for (int j = 0; j < nchunk; ++j) {
+    const int k0 = j * chunk, nk = std::min(chunk, n_cond - k0);
+    double *kap = kappa + (int64_t)k0 * g->n;
+    cudaGraphExec_t gx = nullptr;
+    {
+      // the chunk's view of the per-condition arrays (staging, parameters,
+      // statistics, order): offset by its first condition, restored after
+      const CondView view(c, k0);
+      const std::string key = batch_key(c, nk, mass, cut, g, o, kap, shape);
+      gx = find_graph(c, key);
+      if (!gx) {
+        cudaStream_t user = c->stream;
+        c->stream = c->cap_stream;
+        cudaGraph_t graph = nullptr;
+        helk_status st = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal),
+                                    "graph capture");
+        if (st == HELK_OK) {
+          st = cuda_check(c, cudaMemcpyAsync(c->cond_dev, c->cond_host, nk * sizeof(CondArgs),
+                                             cudaMemcpyHostToDevice, c->stream),
+                          "graph capture");
+          if (st == HELK_OK) st = prepare_lines(c, nk, nullptr, mass, cut, g, o);
+          if (st == HELK_OK) st = run_voigt(c, nk, g, o, kap, shape, tile, ntiles);
+          const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+          if (st == HELK_OK) st = cuda_check(c, e, "graph capture");
+        }
+        c->stream = user;
+        if (st == HELK_OK) st = cuda_check(c, cudaGraphInstantiate(&gx, graph, 0), "graph instantiate");
+        if (graph) cudaGraphDestroy(graph);
+        if (st != HELK_OK) {
+          cudaGetLastError();
+          return st;
+        }
+        keep_graph(c, key, gx);
+      }
+    }
+    HELK_TRY(cuda_check(c, cudaGraphLaunch(gx, c->stream), "graph launch"));
+  }
   stage_end(c, HELK_STAGE_VOIGT);
   HELK_TRY(cuda_check(c, cudaEventRecord(c->cond_ev, c->stream), "opacity_batch"));
   c->last_n = g->n * n_cond;
   c->last_ncond = n_cond;
   c->have_opacity = (kappa == c->kappa);
   c->last_counted_regions = o.count_regions != 0;
+  return HELK_OK;
+}
+
+helk_status helk_set_batch_budget(helk_ctx *c, int64_t bytes) {
+  if (!c) return HELK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (bytes < 0) return set_err(c, HELK_ERR_INVALID_ARG, "set_batch_budget: bytes must be >= 0");
+  c->batch_budget = bytes > 0 ? bytes : HELK_DEFAULT_BATCH_BUDGET;
   return HELK_OK;
 }
 

@@ -12,9 +12,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/helk.h"
+
+// Line-record budget of one chunk of helk_opacity_batch (64 GiB).
+constexpr int64_t HELK_DEFAULT_BATCH_BUDGET = (int64_t)64 << 30;
 
 namespace helk {
 
@@ -159,8 +163,9 @@ struct helk_ctx {
   cudaEvent_t cond_ev = nullptr;   // completion of the last batch that read cond_host
   // CUDA graph of the batched path
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  std::string gkey;
+  std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;  // by call shape, oldest first
+  // line-record bytes one chunk of a batch may use (helk_set_batch_budget)
+  int64_t batch_budget = HELK_DEFAULT_BATCH_BUDGET;
   // opacity output owned by the context
   double *kappa = nullptr;
   int64_t kappa_cap = 0;

@@ -30,8 +30,10 @@ __device__ __forceinline__ float mufu_ex2(float x) {
 }
 
 // KIND: HELK_PROBE_*.  The chains' values stay bounded (x -> a x + b with
-// |a| < 1; x -> 1/x; x -> 2^-|x| in (0, 1]); the final store is conditional
-// on a value the chains never reach, so the work cannot be removed.
+// |a| < 1; x -> 1/(x + b); x -> 2^-|x| in (0, 1]); the final store is
+// conditional on a value the chains never reach, so the work cannot be
+// removed.  The reciprocal probe issues one FP32 addition per reciprocal,
+// which costs issue slots but not MUFU throughput.
 template <int KIND>
 __global__ void __launch_bounds__(PR_THREADS) k_probe(int iters, float a, float b, double ad, double bd,
                                                       float *sink_f, double *sink_d) {
@@ -60,7 +62,9 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int iters, float a, float 
 #pragma unroll
         for (int c = 0; c < PR_CHAINS; ++c) {
           if (KIND == HELK_PROBE_FFMA) x[c] = fmaf(x[c], a, b);
-          if (KIND == HELK_PROBE_MUFU_RCP) x[c] = mufu_rcp(x[c]);
+          // x -> 1/(x + b): an addition between the reciprocals, since the
+          // compiler may fold two reciprocals in a row into nothing
+          if (KIND == HELK_PROBE_MUFU_RCP) x[c] = mufu_rcp(x[c] + b);
           if (KIND == HELK_PROBE_MUFU_EX2) x[c] = mufu_ex2(-fabsf(x[c]));
         }
     }

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("helk_launch_count", _I64, [_P]),
     ("helk_set_tile", ctypes.c_int, [_P, _I32, _I64, _I32]),
     ("helk_peak_probe", ctypes.c_int, [_P, _I32, _P, _P]),
+    ("helk_set_batch_budget", ctypes.c_int, [_P, _I64]),
 ]
 HELK_NSTAGES = 4
 MLP_NPARAMS = 8577
@@ -327,6 +328,10 @@ class Context:
         _check(self.h, lib.helk_transmission(self.h, int(nbins), int(nb), p(sorted_k), p(coeffs), int(ncheb),
                                              int(ng), int(nm), m.ctypes.data_as(_P), p(direct), p(fit)))
         return direct, fit
+
+    def set_batch_budget(self, nbytes):
+        """Line-record bytes one chunk of opacity_batch may use (0: default)."""
+        _check(self.h, lib.helk_set_batch_budget(self.h, int(nbytes)))
 
     def batch_stats(self, n_cond, with_regions=False):
         ev = np.zeros(n_cond, dtype=np.int64)

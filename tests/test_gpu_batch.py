@@ -103,3 +103,31 @@ def test_mixed_species_list(ctx):
     ko, evo, rego = oracle.opacity(mix, case.oracle_cond(), nthreads=NTHREADS)
     assert ev == evo and np.array_equal(reg[:3], rego)
     assert_rel(k, ko, 1e-9, "mixed species")
+
+
+@pytest.mark.parametrize("form", ["f64", "f32"])
+def test_chunked_batch_equals_one_chunk(ctx, form):
+    # a record budget of three conditions' records runs 8 conditions as
+    # chunks of 3, 3 and 2 (each its own graph): the same results bit for bit
+    # and the same per-condition statistics as one chunk, also on a replay
+    from paper_1503_03806_gb300 import helk
+    prec = helk.HELK_PREC_F64 if form == "f64" else helk.HELK_PREC_F32_KAHAN
+    lines = synth.random_lines(2000, 406, 0.0, 200.0, with_elower=True, strengths="lognormal")
+    ctx.upload(lines)
+    T, P, q = conditions(5, 8)
+    k1 = ctx.opacity_batch(T, P, 18.0, CUT, GRID, precision=prec, q_ratio=q, count_regions=True).cpu().numpy()
+    ev1, reg1 = ctx.batch_stats(8, with_regions=True)
+    per_line = 64 if form == "f64" else 120
+    try:
+        ctx.set_batch_budget(3 * 2000 * per_line)
+        for _ in range(2):
+            k3 = ctx.opacity_batch(T, P, 18.0, CUT, GRID, precision=prec, q_ratio=q,
+                                   count_regions=True).cpu().numpy()
+            ev3, reg3 = ctx.batch_stats(8, with_regions=True)
+            assert np.array_equal(k1, k3)
+            assert np.array_equal(ev1, ev3) and np.array_equal(reg1, reg3)
+        ctx.set_batch_budget(1)  # one condition a chunk
+        k8 = ctx.opacity_batch(T, P, 18.0, CUT, GRID, precision=prec, q_ratio=q).cpu().numpy()
+        assert np.array_equal(k1, k8)
+    finally:
+        ctx.set_batch_budget(0)

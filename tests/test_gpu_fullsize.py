@@ -9,7 +9,10 @@ computes one by one.
   1e-8 of its bin maximum).
 - mixed: 4 species x 2.5e7 lines (masses 18, 16, 44, 17 amu, mixing 1/4
   each) in one upload with per-line mass and abundance weight, on the 3e7
-  point grid at 0.001 cm^-1; one condition in the FP32 form.
+  point grid at 0.001 cm^-1: all 16 conditions in one FP32 batch call, then
+  the k-tables of all of them (16000 bins of 30000 points) in one call;
+  sampled points of five conditions, whole bins of four, and the k-tables of
+  those bins (on the oracle's opacity) against the oracle.
 - the largest grid accepted (2^31 - 4097 points), both forms: lines at both
   ends and beyond index 2^30, and, without a cutoff, lines whose centres lie
   outside the int32 range of grid indices.
@@ -149,10 +152,10 @@ def test_largest_grid(ctx):
     torch.cuda.empty_cache()
 
 
-def test_mixed_species_full_size(ctx):
-    import torch
-    from paper_1503_03806_gb300 import helk
-    w = synth.WORKLOADS["mixed"]
+def mixed_lines(w):
+    """The 4-species list of the mixed workload (2.5e7 lines each, masses 18,
+    16, 44, 17 amu, mixing ratio 1/4 each) as one list with per-line mass and
+    abundance weight, ordered by nu0."""
     parts = []
     for s, (m, x) in enumerate(zip(w["species_mass"], w["mixing"])):
         L = synth.workload_lines("mixed", species=s)
@@ -162,26 +165,81 @@ def test_mixed_species_full_size(ctx):
     lines = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
     del parts
     order = np.argsort(lines["nu0"], kind="stable")
-    lines = {k: np.ascontiguousarray(v[order]) for k, v in lines.items()}
-    del order
+    return {k: np.ascontiguousarray(v[order]) for k, v in lines.items()}
+
+
+def test_mixed_batch_full_size(ctx):
+    # The mixed workload as specified: 1e8 lines of 4 species, all 4 T x 4 P
+    # conditions in one helk_opacity_batch call (FP32 form; its records, 120 B
+    # a line and condition, run in chunks under the 64 GiB record budget) on
+    # the 3e7-point grid, then the k-tables of all 16 conditions (16000 bins
+    # of 30000 points, 20 coefficients) in one helk_kdist call.
+    import torch
+    from paper_1503_03806_gb300 import helk
+    w = synth.WORKLOADS["mixed"]
+    lines = mixed_lines(w)
     grid = (w["nu_min"], w["dnu"], w["ngrid"])
-    T, P = w["T"][2], w["P_atm"][2]
-    case = Case(T, P, 18.0, grid, w["cut"], q_ratio=(296.0 / T) ** 1.5)
+    Ts = np.repeat(np.asarray(w["T"]), len(w["P_atm"]))
+    Ps = np.tile(np.asarray(w["P_atm"]), len(w["T"]))
+    qs = (296.0 / Ts) ** 1.5
+    nb = grid[2] // w["nbins"]
     ctx.upload(lines)
-    k = case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN).cpu().numpy()
-    assert np.all(np.isfinite(k)) and k.max() > 0
-    # three regions of 40 points; the oracle gets every line that can reach them
-    rng = np.random.default_rng(5)
+    kb = ctx.opacity_batch(Ts, Ps, 18.0, w["cut"], grid, precision=helk.HELK_PREC_F32_KAHAN, q_ratio=qs)
+    ev, _ = ctx.batch_stats(len(Ts))
+    assert np.all(ev > 0)
     reach = w["cut"][2] + grid[1]
-    cond = case.oracle_cond()
+    rng = np.random.default_rng(5)
 
-    def oracle_at(pts):
-        near = near_lines(lines, grid[0] + pts[0] * grid[1], grid[0] + pts[-1] * grid[1], reach)
-        return oracle.opacity_points(near, cond, pts)[0]
+    def oracle_at(cond):
+        def at(pts):
+            near = near_lines(lines, grid[0] + pts[0] * grid[1], grid[0] + pts[-1] * grid[1], reach)
+            return oracle.opacity_points(near, cond, pts)[0]
+        return at
 
-    for lo in (1000.0, 14000.0, 29000.0):
-        i0 = int((lo - grid[0]) / grid[1])
-        idx = np.sort(rng.choice(np.arange(i0, i0 + 200_000), 40, replace=False))
-        check_sampled_f32(k, w["nbins"], idx, oracle_at, RTOL32, FLOOR, "mixed FP32 at %g" % lo)
-    del lines
+    # sampled points of five conditions (cold and hot, every pressure), two
+    # regions of 30 points each, against the oracle
+    for c in (0, 5, 10, 15, 3):
+        cond = Case(Ts[c], Ps[c], 18.0, grid, w["cut"], q_ratio=qs[c]).oracle_cond()
+        row = kb[c].cpu().numpy()
+        assert np.all(np.isfinite(row)) and row.max() > 0
+        for lo in (3000.0, 21000.0):
+            i0 = int((lo - grid[0]) / grid[1])
+            idx = np.sort(rng.choice(np.arange(i0, i0 + 100_000), 30, replace=False))
+            check_sampled_f32(row, w["nbins"], idx, oracle_at(cond), RTOL32, FLOOR,
+                              "mixed condition %d at %g" % (c, lo))
+        del row
+    # whole bins from the oracle at the two low pressures (cheap there):
+    # the device's opacity of those bins, then the k-tables of the full
+    # 16-condition array with those bins replaced by the oracle's opacity,
+    # against the oracle's own tables (sorted values bit for bit)
+    checks = []
+    for c in (0, 1, 12, 13):
+        cond = Case(Ts[c], Ps[c], 18.0, grid, w["cut"], q_ratio=qs[c]).oracle_cond()
+        for b in (17, 611):
+            pts = np.arange(b * nb, (b + 1) * nb)
+            ko = oracle_at(cond)(pts)
+            got = kb[c, b * nb:(b + 1) * nb].cpu().numpy()
+            thr = FLOOR * ko.max()
+            sel = ko > thr
+            if sel.any():
+                err = np.abs(got[sel] - ko[sel]) / ko[sel]
+                assert err.max() <= RTOL32, ("whole bin", c, b, float(err.max()))
+            assert np.all(np.abs(got[~sel] - ko[~sel]) <= RTOL32 * max(thr, 0.0)), ("below floor", c, b)
+            checks.append((c * w["nbins"] + b, ko))
+    kk = kb.view(-1)
+    for gb, ko in checks:
+        kk[gb * nb:(gb + 1) * nb] = torch.from_numpy(ko).cuda()
+    coef, mean, srt = ctx.kdist(kk, len(Ts) * w["nbins"], w["ncheb"], want_sorted=True)
+    for gb, ko in checks:
+        s_or, c_or, m_or = oracle.kdist(ko, 1, w["ncheb"])
+        assert np.array_equal(srt[gb * nb:(gb + 1) * nb].cpu().numpy(), s_or), gb
+        c = coef[gb].cpu().numpy()
+        assert np.max(np.abs(c - c_or[0])) <= 1e-9 * np.max(np.abs(c_or[0])), gb
+        assert abs(float(mean[gb]) - m_or[0]) <= 1e-12 * abs(m_or[0]) or m_or[0] == float(mean[gb]), gb
+    # every other bin: the sorted output is a non-decreasing permutation of
+    # its input (checked on a sample of bins at full size)
+    for gb in rng.choice(len(Ts) * w["nbins"], 6, replace=False):
+        a = kk[gb * nb:(gb + 1) * nb].cpu().numpy()
+        assert np.array_equal(srt[gb * nb:(gb + 1) * nb].cpu().numpy(), np.sort(a)), gb
+    del kb, kk, srt, lines
     torch.cuda.empty_cache()
