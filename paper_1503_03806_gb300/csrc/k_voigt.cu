@@ -218,17 +218,64 @@ __device__ void f32_drain(F32Pipe &P, int *flags) {
 }
 
 // What one warp needs of one line, prepared by one lane (lanes in parallel)
-// and read by the whole warp with three broadcast loads: the method class of
-// the (line, warp) pair, the covered points, the exact offset
-// d0 = wbase - c (the lane adds its own index), and the method's constants.
+// and read by the whole warp with three broadcast loads: the kind of the
+// (line, warp) pair, the covered points, the point offset, and the method's
+// constants.
+//   Whole-span lines (one method, GH1 or GH3, on every point of the warp's
+//   span, the line centre outside the span): u is stepped from the span edge
+//   nearest the centre, u_k = fma(k - k_b, 32 beta, u_b), one FMA a slot (the
+//   step product is exact, so each u_k is rounded once and |u_b| <= |u_k|
+//   bounds its error by one ulp of u_k); d0 = (float)(base point - c) of lane
+//   0, k_b = 0 (kind *_FWD, centre at or before the span) or NSLOT - 1
+//   (*_BWD, centre at or after it).
+//   The rest (partial cover, a method boundary, the core, or the centre
+//   inside the span): d0 = (float)(wbase - c) and u = (d0 + lane + 32 k) beta
+//   - phi with d0 + lane + 32 k exact, so every point's method (and whether
+//   it is a core point, left to the core kernel) is decided on the same
+//   correctly rounded u as in k_core_f32.
+enum { KIND_MISS = 0, KIND_GH1_FWD = 1, KIND_GH1_BWD = 2, KIND_GH3_FWD = 3, KIND_GH3_BWD = 4, KIND_REST = 5 };
+
 struct __align__(16) WarpLine {
-  int code;          // 0: the line misses the warp; else class | full << 2
-  int lo, hi;        // covered points (grid indices)
-  float d0;          // (float)(wbase - c): exact within 2^24 points of c
+  int kind;          // KIND_*
+  int cls;           // CLS_* (KIND_REST)
+  int lo, hi;        // covered points (grid indices; KIND_REST)
+  float d0;          // point offset of lane 0 at the base slot (see above)
   float beta, nphi, a2;
-  float q0, q1, q2, q3;  // GH1: P1; GH3: C, c3, c45, c2 (Gh3Line); mixed: P1
-  int j;             // the line's index in the chunk
+  float q0, q1, q2, q3;  // GH1: P1; GH3: C, c3, c45, c2 (Gh3Line); rest: P1
 };
+
+// Whole-span lines [t, t1) of one kind: GH1 (4 instructions an evaluation)
+// or GH3 (9), u stepped from the base slot.
+template <int NSLOT, bool FWD, bool GH3>
+__device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, float lanef, int &ngroup,
+                                           float (&sum)[NSLOT], float (&comp)[NSLOT], float (&part)[NSLOT]) {
+  while (t < t1) {
+    const int te = min(t1, t + KAHAN_GROUP - ngroup);
+    ngroup += te - t;
+    for (; t < te; ++t) {
+      const WarpLine &W = wl[t];
+      const float beta = W.beta, a2 = W.a2;
+      const float ub = fmaf(W.d0 + lanef, beta, W.nphi);  // u at the base slot
+      const float h = 32.0f * beta;                        // u step between slots (exact)
+      if (GH3) {
+        const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+          const float u = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
+          part[k] = g3.add(part[k], fmaf(u, u, a2));
+        }
+      } else {
+        const float P1 = W.q0;
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+          const float u = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
+          part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
+        }
+      }
+    }
+    if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
+  }
+}
 
 // MINB resident CTAs per SM: 3 (<= 85 registers a thread) or 2.
 template <int BLOCK, int NSLOT, int LCH, bool COUNT, int MINB>
@@ -340,11 +387,11 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     WarpLine *wl = s_wl[threadIdx.x >> 5];
     const float lanef = (float)lane;
     for (int m0 = 0; m0 < cnum; m0 += 32) {
-    int n1, n13, nall;
+    int nk[5];  // first record of each kind after KIND_GH1_FWD, in kind order
     {
       const int j = m0 + lane;
       WarpLine r;
-      r.code = 0;
+      r.kind = KIND_MISS;
       if (j < cnum) {
         const LineRec32 &L = buf[j];
         const int c = L.c;
@@ -359,15 +406,21 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           const float r2far = fmaxf(fmaf(ul, ul, a2), fmaf(uh, uh, a2));
           const int cls = r2near >= 1.0e6f ? CLS_GH1
                                            : ((r2near >= 100.0f && r2far < 1.0e6f) ? CLS_GH3 : CLS_MIXED);
-          const int full = (lo == wbase) && (hi == wbase + WSPAN - 1);
-          r.code = cls | (full << 2);
+          const bool full = (lo == wbase) && (hi == wbase + WSPAN - 1);
+          r.cls = cls;
           r.lo = lo;
           r.hi = hi;
-          r.d0 = (float)(wbase - c);
           r.beta = beta;
           r.nphi = nphi;
           r.a2 = a2;
-          r.j = j;
+          if (full && cls != CLS_MIXED && (dlo >= 0 || dhi <= 0)) {
+            const bool fwd = dlo >= 0;
+            r.kind = (cls == CLS_GH1 ? KIND_GH1_FWD : KIND_GH3_FWD) + (fwd ? 0 : 1);
+            r.d0 = (float)(fwd ? dlo : dhi - 31);  // lane 0 at slot 0 or NSLOT - 1
+          } else {
+            r.kind = KIND_REST;
+            r.d0 = (float)(wbase - c);
+          }
           if (cls == CLS_GH3) {
             const Gh3Line g3(a2, L.P3);
             r.q0 = g3.C;
@@ -379,61 +432,43 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           }
         }
       }
-      // records ordered by kind: whole-span GH1 lines, whole-span GH3
-      // lines, then the rest; lines that miss the warp are dropped
-      const bool g1 = r.code == (CLS_GH1 | 4), g3 = r.code == (CLS_GH3 | 4);
-      const bool ot = r.code != 0 && !g1 && !g3;
-      const unsigned b1 = __ballot_sync(0xffffffffu, g1), b3 = __ballot_sync(0xffffffffu, g3);
-      const unsigned bo = __ballot_sync(0xffffffffu, ot);
+      // records ordered by kind (lines that miss the warp dropped), each
+      // kind then runs its own class-free loop
+      unsigned b[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) b[q] = __ballot_sync(0xffffffffu, r.kind == q + 1);
       const unsigned lt = (1u << lane) - 1u;
-      n1 = __popc(b1);
-      n13 = n1 + __popc(b3);
-      nall = n13 + __popc(bo);
-      const int pos = g1 ? __popc(b1 & lt) : (g3 ? n1 + __popc(b3 & lt) : n13 + __popc(bo & lt));
-      if (r.code) wl[pos] = r;
+      int pos = 0, run = 0;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (r.kind == q + 1) pos = run + __popc(b[q] & lt);
+        run += __popc(b[q]);
+        nk[q] = run;
+      }
+      if (r.kind != KIND_MISS) {
+        // per-point lines keep their chunk index (their GH3 constants are
+        // formed from the record when needed)
+        if (r.kind == KIND_REST && r.cls == CLS_MIXED) r.q1 = __int_as_float(j);
+        wl[pos] = r;
+      }
     }
     __syncwarp();
-    // whole-span GH1 lines: 5 instructions an evaluation
-    for (int t = 0; t < n1;) {
-      const int te = min(n1, t + KAHAN_GROUP - ngroup);
-      ngroup += te - t;
-      for (; t < te; ++t) {
-        const WarpLine &W = wl[t];
-        const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2, P1 = W.q0;
-#pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-          const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-          part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
-        }
-        if (COUNT) cnt[2] += NSLOT;
-      }
-      if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
-    }
-    // whole-span GH3 lines: 10 instructions an evaluation
-    for (int t = n1; t < n13;) {
-      const int te = min(n13, t + KAHAN_GROUP - ngroup);
-      ngroup += te - t;
-      for (; t < te; ++t) {
-        const WarpLine &W = wl[t];
-        const float d0 = W.d0 + lanef, beta = W.beta, nphi = W.nphi, a2 = W.a2;
-        const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
-#pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-          const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-          part[k] = g3.add(part[k], fmaf(u, u, a2));
-        }
-        if (COUNT) cnt[1] += NSLOT;
-      }
-      if (ngroup == KAHAN_GROUP) kahan_fold<NSLOT>(ngroup, sum, comp, part);
+    span_lines<NSLOT, true, false>(wl, 0, nk[0], lanef, ngroup, sum, comp, part);
+    span_lines<NSLOT, false, false>(wl, nk[0], nk[1], lanef, ngroup, sum, comp, part);
+    span_lines<NSLOT, true, true>(wl, nk[1], nk[2], lanef, ngroup, sum, comp, part);
+    span_lines<NSLOT, false, true>(wl, nk[2], nk[3], lanef, ngroup, sum, comp, part);
+    if (COUNT) {
+      cnt[2] += (unsigned long long)NSLOT * nk[1];
+      cnt[1] += (unsigned long long)NSLOT * (nk[3] - nk[1]);
     }
     // the rest: GH1 or GH3 lines covering part of the span, and lines with a
-    // method boundary or their core in the span
-    for (int jj = n13; jj < nall;) {
-      const int je = min(nall, jj + KAHAN_GROUP - ngroup);
+    // method boundary, their core or their centre in the span
+    for (int jj = nk[3]; jj < nk[4];) {
+      const int je = min(nk[4], jj + KAHAN_GROUP - ngroup);
       ngroup += je - jj;
       for (; jj < je; ++jj) {
         const WarpLine &W = wl[jj];
-        const int cls = W.code & 3;
+        const int cls = W.cls;
         const int lo = W.lo, hi = W.hi;
         const float beta = W.beta, nphi = W.nphi, a2 = W.a2;
         // (i - c) of this lane's first point, exact in FP32
@@ -463,7 +498,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
         } else {
           // Per point: GH1 or GH3; core points (r^2 < 100) are left to the
           // core kernel (k_core_f32).
-          const int j = W.j;
+          const int j = __float_as_int(W.q1);
           const float P1 = W.q0;
           const Gh3Line g3(a2, buf[j].P3);
 #pragma unroll
@@ -574,9 +609,20 @@ __global__ void __launch_bounds__(256)
   const double scale = ldexp(weight, cst[cond].scale_exp);
   const float *kcore = kcore_all + (int64_t)cond * ngrid;
   double *kappa = kappa_all + (int64_t)cond * ngrid;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ngrid; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = kcore[i];
-    if (v != 0.0f) kappa[i] += scale * (double)v;
+  // four points a thread per pass, their loads issued together
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < ngrid; i0 += 4 * stride) {
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + q * stride;
+      v[q] = i < ngrid ? kcore[i] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + q * stride;
+      if (v[q] != 0.0f) kappa[i] += scale * (double)v[q];
+    }
   }
 }
 
