@@ -148,7 +148,7 @@ void helk_destroy(helk_ctx *c) {
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
                   c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->ckey32, c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
-                  c->mean_dev, c->tmp};
+                  c->mean_dev, c->tmp, c->kd_fold, c->kd_part};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (c->stats_host) cudaFreeHost(c->stats_host);
@@ -734,7 +734,7 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
   HELK_TRY(bind_device(c));
   if (c->pinv_nb != nb || c->pinv_ncheb != ncheb || !c->pinv) {
     HELK_TRY(ensure_buf(c, (void **)&c->pinv, &c->pinv_cap, pinv_bytes(nb, ncheb), "kdist pseudo-inverse"));
-    HELK_TRY(ensure_buf(c, &c->tmp, &c->tmp_cap, nb * ncheb * 8, "kdist pseudo-inverse"));
+    HELK_TRY(ensure_buf(c, &c->tmp, &c->tmp_cap, pinv_work_doubles(nb, ncheb) * 8, "kdist pseudo-inverse"));
     stage_begin(c, HELK_STAGE_SETUP);
     HELK_TRY(cuda_check(c, launch_pinv(c, nb, ncheb, (double *)c->tmp), "kdist pseudo-inverse"));
     stage_end(c, HELK_STAGE_SETUP);
@@ -753,6 +753,8 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
       c->sort_cap = n * 8;
     }
   }
+  HELK_TRY(ensure_buf(c, &c->kd_fold, &c->kd_fold_cap, kdist_fold_bytes(n, nbins), "kdist scratch"));
+  HELK_TRY(ensure_buf(c, &c->kd_part, &c->kd_part_cap, kdist_part_bytes(c, n, nbins), "kdist scratch"));
   double *cdst = coeffs, *mdst = mean;
   if (out_on_host) {
     HELK_TRY(ensure_buf(c, (void **)&c->coef_dev, &c->coef_cap, (int64_t)nbins * ncheb * 8, "kdist out"));

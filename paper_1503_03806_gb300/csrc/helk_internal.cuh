@@ -178,6 +178,8 @@ struct helk_ctx {
   double *pinv = nullptr;  // pseudo-inverse of the Chebyshev design matrix
   int64_t pinv_cap = 0, pinv_nb = 0;
   int pinv_ncheb = 0;
+  void *kd_fold = nullptr, *kd_part = nullptr;  // fit stage: folded logarithms, partial sums
+  int64_t kd_fold_cap = 0, kd_part_cap = 0;
   double *coef_dev = nullptr, *mean_dev = nullptr;
   int64_t coef_cap = 0, mean_cap = 0;
   // Voigt surrogate network (k_mlp.cu): FP32 parameters, Adam moments,
@@ -346,10 +348,14 @@ cudaError_t launch_voigt_f64(helk_ctx *c, int n_cond, const helk_grid &g, const 
 cudaError_t launch_selftest_timeout(helk_ctx *c, int limit_us);
 // k_kdist.cu
 int64_t pinv_bytes(int64_t nb, int ncheb);
+int64_t pinv_work_doubles(int64_t nb, int ncheb);
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work);
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
                               double kappa_floor, double *coef, double *mean, double *kg_out);
 int64_t kdist_smem_max_points(helk_ctx *c);
+// scratch of the fit stage: folded logarithms, per-group partial sums
+int64_t kdist_fold_bytes(int64_t n, int nbins);
+int64_t kdist_part_bytes(helk_ctx *c, int64_t n, int nbins);
 // k_mlp.cu
 constexpr int MLP_NPARAMS_H = 8577;
 cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const double *x, const double *y,

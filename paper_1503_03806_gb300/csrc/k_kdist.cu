@@ -112,6 +112,12 @@ __device__ __forceinline__ float2 log_ff(unsigned long long b, const float2 *lnc
 }
 
 // ------------------------------------------------------ pseudo-inverse --
+// Position of P[k][j] (j < ceil(N_b/2)) in the blocked layout of the
+// symmetrized half: blocks of 32 columns, each [k][32].
+__host__ __device__ __forceinline__ int64_t pinv_index(int k, int64_t j, int ncheb) {
+  return ((j >> 5) * ncheb + k) * 32 + (j & 31);
+}
+constexpr int PINV_MIN_COLS = 64;  // buffers hold max(N_b, 64) columns
 // The design matrix A_jk = T_k(t_j), t_j = (2j+1)/N_b - 1, is the same for
 // every bin, so its pseudo-inverse P = R^{-1} Q_1^T (Householder QR, A = QR)
 // is computed once per (N_b, n_cheb) and each bin's coefficients are
@@ -217,21 +223,28 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
   __syncthreads();
   // The abscissae are symmetric, t_{nb-1-j} = -t_j, and T_k(-t) = (-1)^k T_k(t),
   // so P[k][nb-1-j] = (-1)^k P[k][j]: only the symmetrized first half,
-  // j < nh = ceil(nb/2), is kept, as FP32 (high, low) pairs [k][nh], built in
-  // `work` and then moved to the front of P.
+  // j < nh = ceil(nb/2), is kept, as FP32 (high, low) pairs in blocks of 32
+  // columns, [j / 32][k][j % 32] (pinv_index; columns past nh are zero), so
+  // that any run of whole blocks is one contiguous copy; built in `work` and
+  // then moved to the front of P.
   const int64_t nh = (nb + 1) / 2;
+  const int64_t npad = ((nh + 31) / 32) * 32;
   float2 *W = reinterpret_cast<float2 *>(work);
-  for (int64_t e = tid; e < (int64_t)ncheb * nh; e += PI_THREADS) {
-    const int k = (int)(e / nh);
-    const int64_t j = e % nh;
-    const double v =
-        0.5 * (P[(int64_t)k * nb + j] + ((k & 1) ? -1.0 : 1.0) * P[(int64_t)k * nb + (nb - 1 - j)]);
-    const float hi = (float)v;
-    W[e] = make_float2(hi, (float)(v - (double)hi));
+  for (int64_t e = tid; e < (int64_t)ncheb * npad; e += PI_THREADS) {
+    const int k = (int)(e / npad);
+    const int64_t j = e % npad;
+    float2 v2 = make_float2(0.0f, 0.0f);
+    if (j < nh) {
+      const double v =
+          0.5 * (P[(int64_t)k * nb + j] + ((k & 1) ? -1.0 : 1.0) * P[(int64_t)k * nb + (nb - 1 - j)]);
+      const float hi = (float)v;
+      v2 = make_float2(hi, (float)(v - (double)hi));
+    }
+    W[pinv_index(k, j, ncheb)] = v2;
   }
   __syncthreads();
   float2 *Ps = reinterpret_cast<float2 *>(P);
-  for (int64_t e = tid; e < (int64_t)ncheb * nh; e += PI_THREADS) Ps[e] = W[e];
+  for (int64_t e = tid; e < (int64_t)ncheb * npad; e += PI_THREADS) Ps[e] = W[e];
   if (tid == 0 && vtv_out) vtv_out[0] = vtv[0];
   // the logarithm's table, ln c_j and 1/c_j (c_j = 1 + j/128) as FP32
   // (high, low) pairs, computed here once instead of in every bin's CTA
@@ -247,12 +260,15 @@ __global__ void __launch_bounds__(PI_THREADS) k_pinv(int64_t nb, int ncheb, doub
   }
 }
 
-// The pseudo-inverse buffer: nb ncheb doubles of work space (the
-// symmetrized half of P at its front when done), then the logarithm's table.
-int64_t pinv_bytes(int64_t nb, int ncheb) { return (nb * ncheb + KD_LNTAB) * 8; }
+// The pseudo-inverse buffer: max(nb, 64) ncheb doubles of work space (the
+// blocked symmetrized half of P at its front when done; it takes at most
+// ncheb (ceil(nb/2) + 31) FP32 pairs), then the logarithm's table.  The
+// Householder work array k_pinv is given has the same size.
+int64_t pinv_work_doubles(int64_t nb, int ncheb) { return std::max<int64_t>(nb, PINV_MIN_COLS) * ncheb; }
+int64_t pinv_bytes(int64_t nb, int ncheb) { return (pinv_work_doubles(nb, ncheb) + KD_LNTAB) * 8; }
 
 static float2 *pinv_lntab(helk_ctx *c, int64_t nb, int ncheb) {
-  return reinterpret_cast<float2 *>(c->pinv + nb * ncheb);
+  return reinterpret_cast<float2 *>(c->pinv + pinv_work_doubles(nb, ncheb));
 }
 
 cudaError_t launch_pinv(helk_ctx *c, int64_t nb, int ncheb, double *work) {
@@ -619,12 +635,16 @@ __device__ __forceinline__ float2 ff_warp_sum8(const float2 (&v)[8], int lane) {
 // arrays: bucket sort, else register-resident radix passes); MODE 1: keys in
 // the global ping-pong
 // buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
+// With Lf != NULL the bin's fit is left to k_kdist_fit: the kernel writes
+// the folded logarithms (L_j + L_{nb-1-j}, L_j - L_{nb-1-j}) for j < nh, as
+// float-float pairs, to Lf[bin * npad + j] (npad = nh rounded up to 32) and
+// no coefficients; else it fits the bin itself from P in global memory.
 template <int MODE>
 __global__ void __launch_bounds__(KD_THREADS)
     k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
                 const float2 *__restrict__ P, const float2 *__restrict__ lntab, unsigned long long *gA,
                 unsigned long long *gB, double *__restrict__ coef, double *__restrict__ mean,
-                double *__restrict__ kg_out) {
+                double *__restrict__ kg_out, float4 *__restrict__ Lf) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t hist[KD_HIST];
   __shared__ uint32_t wtot[32];
@@ -691,12 +711,33 @@ __global__ void __launch_bounds__(KD_THREADS)
   float2 *Ls = reinterpret_cast<float2 *>(S);
   const unsigned long long floor_bits = (unsigned long long)__double_as_longlong(kappa_floor);
   __syncthreads();  // every thread has read kmax before L_j overwrites the keys
-  for (int j = tid; j < nb; j += KD_THREADS) {
-    const unsigned long long kb = S[j];
-    if (kg_out) kg_out[off + j] = __longlong_as_double((long long)kb);
-    fx_add(fx_lo, fx_hi, kb, emax, fxb);
-    // non-negative doubles order as their bit patterns: max(k, floor) on the bits
-    Ls[j] = log_ff(kb > floor_bits ? kb : floor_bits, s_lnc, s_invc);
+  // four points a thread per pass: their keys are read before any L_j is
+  // written in place, so the four logarithms run side by side (the integer
+  // bin sum does not depend on the order)
+  constexpr int LU = 4;
+  for (int j0 = tid; j0 < nb; j0 += LU * KD_THREADS) {
+    unsigned long long kq[LU];
+#pragma unroll
+    for (int q = 0; q < LU; ++q) {
+      const int j = j0 + q * KD_THREADS;
+      kq[q] = j < nb ? S[j] : 0ull;
+    }
+    float2 lq[LU];
+#pragma unroll
+    for (int q = 0; q < LU; ++q) {
+      const int j = j0 + q * KD_THREADS;
+      if (j < nb) {
+        if (kg_out) kg_out[off + j] = __longlong_as_double((long long)kq[q]);
+        fx_add(fx_lo, fx_hi, kq[q], emax, fxb);
+      }
+      // non-negative doubles order as their bit patterns: max(k, floor) on the bits
+      lq[q] = log_ff(kq[q] > floor_bits ? kq[q] : floor_bits, s_lnc, s_invc);
+    }
+#pragma unroll
+    for (int q = 0; q < LU; ++q) {
+      const int j = j0 + q * KD_THREADS;
+      if (j < nb) Ls[j] = lq[q];
+    }
   }
   fx_warp_sum(fx_lo, fx_hi);
   if (lane == 0) {
@@ -704,47 +745,59 @@ __global__ void __launch_bounds__(KD_THREADS)
     red_fx[w][1] = fx_hi;
   }
   __syncthreads();
-  // c = P L, eight coefficients per sweep over the first half of the points:
-  // c_k = sum_{j < nh} P[k][j] (L_j + (-1)^k L_{nb-1-j}) (the middle point of
-  // an odd bin once), P holding the symmetrized half [k][nh]
   const int nh = (nb + 1) >> 1;
-  for (int k0 = 0; k0 < ncheb; k0 += 8) {
-    float sh[8], sl[8];
+  if (Lf) {
+    // folded logarithms for k_kdist_fit (the middle point of an odd bin
+    // once, in both halves of its pair)
+    const int npad = ((nh + 31) >> 5) << 5;
+    float4 *out = Lf + (int64_t)blockIdx.x * npad;
+    for (int jj = tid; jj < npad; jj += KD_THREADS) {
+      float2 Lp = make_float2(0.0f, 0.0f), Lm = Lp;
+      if (jj < nh) fold_pair(Ls, nb, jj, Lp, Lm);
+      out[jj] = make_float4(Lp.x, Lp.y, Lm.x, Lm.y);
+    }
+  } else {
+    // c = P L, eight coefficients per sweep over the first half of the
+    // points: c_k = sum_{j < nh} P[k][j] (L_j + (-1)^k L_{nb-1-j}) (the
+    // middle point of an odd bin once), P the blocked symmetrized half
+    for (int k0 = 0; k0 < ncheb; k0 += 8) {
+      float sh[8], sl[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
-    // two points a step, so that 16 loads of P are in flight per thread
-    for (int j = tid; j < nh; j += 2 * KD_THREADS) {
-      const int j2 = j + KD_THREADS;
-      float2 Pa[8], Pb[8];
+      for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
+      // two points a step, so that 16 loads of P are in flight per thread
+      for (int jj = tid; jj < nh; jj += 2 * KD_THREADS) {
+        const int j2 = jj + KD_THREADS;
+        float2 Pa[8], Pb[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        Pa[q] = k0 + q < ncheb ? P[(int64_t)(k0 + q) * nh + j] : make_float2(0.0f, 0.0f);
-        Pb[q] = (k0 + q < ncheb && j2 < nh) ? P[(int64_t)(k0 + q) * nh + j2] : make_float2(0.0f, 0.0f);
-      }
-      float2 Lp, Lm;
-      fold_pair(Ls, nb, j, Lp, Lm);
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pa[q], (q & 1) ? Lm : Lp);
-      if (j2 < nh) {
-        fold_pair(Ls, nb, j2, Lp, Lm);
+        for (int q = 0; q < 8; ++q) {
+          Pa[q] = k0 + q < ncheb ? P[pinv_index(k0 + q, jj, ncheb)] : make_float2(0.0f, 0.0f);
+          Pb[q] = (k0 + q < ncheb && j2 < nh) ? P[pinv_index(k0 + q, j2, ncheb)] : make_float2(0.0f, 0.0f);
+        }
+        float2 Lp, Lm;
+        fold_pair(Ls, nb, jj, Lp, Lm);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pb[q], (q & 1) ? Lm : Lp);
-      }
-    }
-    float2 v[8];
+          if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pa[q], (q & 1) ? Lm : Lp);
+        if (j2 < nh) {
+          fold_pair(Ls, nb, j2, Lp, Lm);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float h, l;
-      two_sum_f(sh[q], sl[q], h, l);
-      v[q] = make_float2(h, l);
+          for (int q = 0; q < 8; ++q)
+            if (k0 + q < ncheb) dfma_acc(sh[q], sl[q], Pb[q], (q & 1) ? Lm : Lp);
+        }
+      }
+      float2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float h, l;
+        two_sum_f(sh[q], sl[q], h, l);
+        v[q] = make_float2(h, l);
+      }
+      const float2 r = ff_warp_sum8(v, lane);
+      if ((lane & 3) == 0 && k0 + (lane >> 2) < ncheb) red[w][k0 + (lane >> 2)] = r;
     }
-    const float2 r = ff_warp_sum8(v, lane);
-    if ((lane & 3) == 0 && k0 + (lane >> 2) < ncheb) red[w][k0 + (lane >> 2)] = r;
   }
   __syncthreads();
-  if (tid < ncheb) {
+  if (!Lf && tid < ncheb) {
     float2 s = red[0][tid];
     for (int i = 1; i < KD_WARPS; ++i) s = ff_add(s, red[i][tid]);
     coef[(int64_t)blockIdx.x * ncheb + tid] = (double)s.x + (double)s.y;
@@ -764,6 +817,98 @@ __global__ void __launch_bounds__(KD_THREADS)
   }
 }
 
+// --------------------------------------------------------------- the fit --
+// c = P L for many bins at once: a CTA takes KF_BINS bins (one warp each)
+// and one group of P's column blocks, stages P's columns through shared
+// memory one chunk of KF_COLS at a time and applies each chunk to all its
+// bins, so P is read from L2 once per KF_BINS bins (instead of once per bin);
+// every lane accumulates the ncheb coefficients of its bin over its columns
+// in double-float (dfma_acc), the warp reduces them, and the partial sums of
+// the column groups go to `part` ([group][bin][k]), added in a fixed order by
+// k_kdist_fit_sum.
+constexpr int KF_BINS = 8;
+constexpr int KF_THREADS = 32 * KF_BINS;
+constexpr int KF_COLS = 64;  // columns (two 32-column blocks of P) per chunk
+
+__global__ void __launch_bounds__(KF_THREADS)
+    k_kdist_fit(const float4 *__restrict__ Lf, int npad, int nh, int nbins, int ncheb,
+                const float2 *__restrict__ P, int cols_per_group, float2 *__restrict__ part) {
+  __shared__ float2 Pst[NCHEB_MAX * KF_COLS];  // [32-column block][k][32]
+  __shared__ float2 wred[KF_BINS][NCHEB_MAX];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int g = blockIdx.x;
+  const int bin = blockIdx.y * KF_BINS + w;
+  const int c0 = g * cols_per_group, c1 = min(npad, c0 + cols_per_group);
+  const float4 *lrow = Lf + (int64_t)min(bin, nbins - 1) * npad;
+  float sh[NCHEB_MAX], sl[NCHEB_MAX];
+#pragma unroll
+  for (int k = 0; k < NCHEB_MAX; ++k) sh[k] = sl[k] = 0.0f;
+  for (int cc = c0; cc < c1; cc += KF_COLS) {
+    const int ncol = min(KF_COLS, c1 - cc);  // a multiple of 32
+    // the chunk of P: whole 32-column blocks, contiguous in the blocked layout
+    const float2 *src = P + (int64_t)(cc >> 5) * ncheb * 32;
+    for (int e = tid; e < ncol * ncheb; e += KF_THREADS) Pst[e] = src[e];
+    __syncthreads();
+    if (bin < nbins) {
+      for (int b = 0; b < (ncol >> 5); ++b) {
+        const int j = cc + 32 * b + lane;
+        const float4 l = lrow[j];  // zero past nh
+        const float2 Lp = make_float2(l.x, l.y), Lm = make_float2(l.z, l.w);
+        const float2 *pb = Pst + b * ncheb * 32 + lane;
+#pragma unroll
+        for (int k = 0; k < NCHEB_MAX; ++k)
+          if (k < ncheb) dfma_acc(sh[k], sl[k], pb[k * 32], (k & 1) ? Lm : Lp);
+      }
+    }
+    __syncthreads();
+  }
+  // warp sums, eight coefficients at a time (reduce-scatter)
+#pragma unroll
+  for (int k0 = 0; k0 < NCHEB_MAX; k0 += 8) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float h, l;
+      two_sum_f(sh[k0 + q], sl[k0 + q], h, l);
+      v[q] = make_float2(h, l);
+    }
+    const float2 r = ff_warp_sum8(v, lane);
+    if ((lane & 3) == 0) wred[w][k0 + (lane >> 2)] = r;
+  }
+  __syncwarp();
+  if (bin < nbins && lane < ncheb)
+    part[((int64_t)g * nbins + bin) * ncheb + lane] = wred[w][lane];
+}
+
+// coef[b][k] = sum over the column groups of the partial sums, in group order
+__global__ void k_kdist_fit_sum(const float2 *__restrict__ part, int ngroups, int nbins, int ncheb,
+                                double *__restrict__ coef) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nbins * ncheb) return;
+  float2 s = part[e];
+  for (int g = 1; g < ngroups; ++g) s = ff_add(s, part[(int64_t)g * nbins * ncheb + e]);
+  coef[e] = (double)s.x + (double)s.y;
+}
+
+int64_t kdist_fold_bytes(int64_t n, int nbins) {
+  const int64_t nb = n / nbins, nh = (nb + 1) / 2, npad = (nh + 31) / 32 * 32;
+  return (int64_t)nbins * npad * 16;
+}
+
+// Column groups of the fit: enough CTAs for two per SM, each group at least
+// two chunks wide.
+static int fit_groups(helk_ctx *c, int npad, int nbins) {
+  const int bingroups = (nbins + KF_BINS - 1) / KF_BINS;
+  const int want = std::max(1, (2 * c->num_sms + bingroups - 1) / bingroups);
+  const int most = std::max(1, npad / (2 * KF_COLS));
+  return std::min(want, most);
+}
+
+int64_t kdist_part_bytes(helk_ctx *c, int64_t n, int nbins) {
+  const int64_t nb = n / nbins, nh = (nb + 1) / 2, npad = (nh + 31) / 32 * 32;
+  return (int64_t)fit_groups(c, (int)npad, nbins) * nbins * NCHEB_MAX * 8;
+}
+
 int64_t kdist_smem_max_points(helk_ctx *c) {
   // two shared-memory key arrays (16 B a point) beside ~26 KB of static smem
   const int64_t fixed = 26 * 1024;
@@ -776,6 +921,7 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   const int nb = (int)(n / nbins);
   const float2 *P = reinterpret_cast<const float2 *>(c->pinv);
   const float2 *lntab = pinv_lntab(c, nb, ncheb);
+  float4 *Lf = reinterpret_cast<float4 *>(c->kd_fold);
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
     const size_t smem = (size_t)nb * 16;
     cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -783,12 +929,26 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
     if (e != cudaSuccess) return e;
     ++c->launches;
     k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
-                                                           nullptr, nullptr, coef, mean, kg_out);
+                                                           nullptr, nullptr, coef, mean, kg_out, Lf);
   } else {
     ++c->launches;
     k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
-                                                        c->sort_a, c->sort_b, coef, mean, kg_out);
+                                                        c->sort_a, c->sort_b, coef, mean, kg_out, Lf);
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nh = (nb + 1) / 2, npad = (nh + 31) / 32 * 32;
+  const int groups = fit_groups(c, npad, nbins);
+  const int cpg = ((npad / 32 + groups - 1) / groups) * 32;
+  float2 *part = reinterpret_cast<float2 *>(c->kd_part);
+  ++c->launches;
+  k_kdist_fit<<<dim3(groups, (nbins + KF_BINS - 1) / KF_BINS), KF_THREADS, 0, c->stream>>>(
+      Lf, npad, nh, nbins, ncheb, P, cpg, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ++c->launches;
+  const int64_t ne = (int64_t)nbins * ncheb;
+  k_kdist_fit_sum<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(part, groups, nbins, ncheb, coef);
   return cudaGetLastError();
 }
 
@@ -945,6 +1105,6 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
   k_kdist_bin<0><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor,
                                                   reinterpret_cast<const float2 *>(ptr),
                                                   reinterpret_cast<const float2 *>(ptr + 2 * KDIST_STATIC_PINV),
-                                                  nullptr, nullptr, coeffs, mean, kg_out);
+                                                  nullptr, nullptr, coeffs, mean, kg_out, nullptr);
   return cudaGetLastError() == cudaSuccess ? HELK_OK : HELK_ERR_CUDA;
 }

@@ -66,7 +66,7 @@ __device__ __forceinline__ unsigned long long surr_reserve(SurrQueue *sq) {
 // appending the point to the surrogate's queue when its cell is validated
 // (the queue's kernel adds it later).
 __device__ __forceinline__ float core_point(const LineRec32 &L, float x, int i, int srow, SurrQueue *sq,
-                                         int cond) {
+                                         int cond, const float *w) {
   if (srow >= 0 && surr_route(sq, srow, x)) {
     const unsigned long long slot = surr_reserve(sq);
     if (slot < sq->cap) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ float core_point(const LineRec32 &L, float x, int i, 
       return 0.0f;
     }
   }
-  return L.Sp * k916_f32(x, L.a, L.erfcx_a, L.sig1);
+  return L.Sp * k916_f32(x, L.a, L.erfcx_a, L.sig1, w);
 }
 
 // Hardware reciprocal approximation (max relative error ~1 ulp); every
@@ -555,29 +555,41 @@ __global__ void __launch_bounds__(CORE_BLOCK)
     k_core_f32(const LineRec32 *__restrict__ rec_all, const int2 *__restrict__ core_all, int64_t nlines,
                const int32_t *__restrict__ ckey, int ngrid, float *__restrict__ kcore_all, CondStats *cst,
                SurrQueue *sq) {
+  // per warp: the series weights of the line being evaluated
+  __shared__ float s_w[CORE_BLOCK / 32][32];
   const int cond = blockIdx.y;
   const int cw1 = cst[cond].core_w1;
   if (cw1 == 0) return;  // no line of the condition has a core (k_core_add skips it too)
   // each warp finds its own 32 points' candidate lines: no CTA barrier
   const int64_t A = (int64_t)blockIdx.x * CORE_BLOCK + (threadIdx.x & ~31);
   if (A >= ngrid) return;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  float *w = s_w[threadIdx.x >> 5];
   const int64_t B = min(A + 32, (int64_t)ngrid);
   const int64_t W = cw1 - 1;  // integer searches (FP64 is the scarce unit here)
   const int64_t first = warp_search(ckey, 0, nlines, A - W, false);
   const int64_t last = warp_search(ckey, first, nlines, B - 1 + W, true);
   const LineRec32 *rec = rec_all + (int64_t)cond * nlines;
   const int2 *core = core_all + (int64_t)cond * nlines;
-  const int i = (int)(A + (threadIdx.x & 31));
+  const int i = (int)(A + lane);
   float v = 0.0f;
   unsigned long long n916 = 0, nterm = 0;
-  if (i < ngrid) {
-    for (int64_t l = first; l < last; ++l) {
-      const int2 cr = core[l];  // the line's core points, a superset of r^2 < 100
-      if (i < cr.x || i > cr.y) continue;
-      const LineRec32 &L = rec[l];
-      const float u = fmaf((float)(i - L.c), L.beta, -L.phi_k);
-      if (fmaf(u, u, L.a2) >= 100.0f) continue;
-      v += core_point(L, fabsf(u), i, surr_row(sq, L.a), sq, cond);
+  // the line loop is warp-uniform: each line's weight table is built by the
+  // whole warp when any lane's point lies in its core
+  for (int64_t l = first; l < last; ++l) {
+    const int2 cr = core[l];  // the line's core points, a superset of r^2 < 100
+    bool in = i < ngrid && i >= cr.x && i <= cr.y;
+    float u = 0.0f;
+    const LineRec32 &L = rec[l];
+    if (in) {
+      u = fmaf((float)(i - L.c), L.beta, -L.phi_k);
+      in = fmaf(u, u, L.a2) < 100.0f;
+    }
+    if (!__any_sync(0xffffffffu, in)) continue;
+    w[lane] = a916_weight_f32(lane + 1, L.a2);
+    __syncwarp();
+    if (in) {
+      v += core_point(L, fabsf(u), i, surr_row(sq, L.a), sq, cond, w);
       if (COUNT) {
         int n0, n1;
         a916_range_f32(fabsf(u), n0, n1);
@@ -585,14 +597,15 @@ __global__ void __launch_bounds__(CORE_BLOCK)
         nterm += (unsigned long long)(n1 - n0 + 1);
       }
     }
-    kcore_all[(int64_t)cond * ngrid + i] = v;
+    __syncwarp();  // the table is rebuilt for the next line
   }
+  if (i < ngrid) kcore_all[(int64_t)cond * ngrid + i] = v;
   if (COUNT) {
     for (int o = 16; o > 0; o >>= 1) {
       n916 += __shfl_down_sync(0xffffffffu, n916, o);
       nterm += __shfl_down_sync(0xffffffffu, nterm, o);
     }
-    if ((threadIdx.x & 31) == 0 && n916) {
+    if (lane == 0 && n916) {
       atomicAdd(&cst[cond].region[0], n916);
       atomicAdd(&cst[cond].region[3], nterm);
     }

@@ -57,7 +57,7 @@ static __device__ __noinline__ double k916_f64(double x, double y, double erfcx_
   return K;
 }
 
-// The same series in FP32 (accurate expf/sincosf).  Only the terms within
+// The same series in FP32.  Only the terms within
 // A916_TAIL_F32 = 4.3 of the Gaussian peaks are summed (each dropped term is
 // below e^{-18.49} = 9.3e-9 of its weight): the truncation is below 3e-9 of K
 // over x^2 + y^2 < 100, y >= 1e-8 (against the exact w(z), in FP64), under
@@ -75,7 +75,21 @@ static __device__ __forceinline__ void a916_range_f32(float x, int &n0, int &n1)
   n1 = (int)floorf((x + A916_TAIL_F32) * 2.0f);
 }
 
-static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y, float sig1) {
+// The series weights 1/((nh)^2 + y^2) of one line, n = 1..A916_NMAX_F32:
+// every term of a window within A916_TAIL_F32 of x < 10 has
+// n <= 2 (10 + 4.3) < A916_NMAX_F32.  Lane l of a warp computes n = l + 1,
+// so a warp fills a line's table with one reciprocal a lane.
+constexpr int A916_NMAX_F32 = 29;
+static __device__ __forceinline__ float a916_weight_f32(int n, float y2) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaf((float)(n * n), 0.25f, y2)));
+  return r;
+}
+
+// Algorithm 916 in FP32 (accurate expf/sincosf) with the line's series
+// weights from a table, w[n - 1] = 1/((nh)^2 + y^2): each term is then one
+// FMA (and the two ratio updates), with no reciprocal of its own.
+static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y, float sig1, const float *w) {
   const float h = 0.5f;
   const float ex2 = expf(-(x * x));
   const float xy = x * y;
@@ -89,12 +103,12 @@ static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y
   int n0, n1;
   a916_range_f32(x, n0, n1);
   const float q = 0.60653065971f;  // e^{-2h^2}
-  float nhn = n0 * h;
-  const float dm = nhn - x, dp = nhn + x;
+  const float nh0 = n0 * h;
+  const float dm = nh0 - x, dp = nh0 + x;
   float E3 = expf(-(dm * dm));
   float R3 = expf(-(2.0f * h * dm + h * h));
   float s23 = 0.0f;
-  const float y2 = y * y;
+  const float *wn = w + (n0 - 1);
   // Beyond x = A916_TAIL_F32 - h every S2 term e^{-(nh+x)^2}, n >= 1, is
   // below e^{-18.49} (outside the window): when that holds for all the
   // warp's active lanes, the S2 recurrence is left out (a warp-uniform
@@ -104,29 +118,26 @@ static __device__ __forceinline__ float k916_f32(float x, float y, float erfcx_y
   if (__all_sync(__activemask(), x > A916_TAIL_F32 - h)) {
 #pragma unroll 6
     for (int t = 0; t < A916_TERMS_F32; ++t) {
-      s23 += __fdividef(E3, fmaf(nhn, nhn, y2));
+      s23 = fmaf(E3, wn[t], s23);
       E3 *= R3;
       R3 *= q;
-      nhn += h;
     }
   } else {
     float E2 = expf(-(dp * dp));
     float R2 = expf(-(2.0f * h * dp + h * h));
 #pragma unroll 4
     for (int t = 0; t < A916_S2_TERMS_F32; ++t) {
-      s23 += __fdividef(E2 + E3, fmaf(nhn, nhn, y2));
+      s23 = fmaf(E2 + E3, wn[t], s23);
       E3 *= R3;
       R3 *= q;
       E2 *= R2;
       R2 *= q;
-      nhn += h;
     }
 #pragma unroll 5
     for (int t = A916_S2_TERMS_F32; t < A916_TERMS_F32; ++t) {
-      s23 += __fdividef(E3, fmaf(nhn, nhn, y2));
+      s23 = fmaf(E3, wn[t], s23);
       E3 *= R3;
       R3 *= q;
-      nhn += h;
     }
   }
   const float k2h = 0.31830988618f;  // 2h/pi
