@@ -441,6 +441,7 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
 // more than KD_BUCKET_MAX keys this returns false with A untouched, and the
 // caller radix-sorts instead.
 constexpr int KD_NBUCKET = KD_THREADS * 8;  // block_exscan_4096's counters
+static_assert(KD_NBUCKET == 4096, "the bucket passes use block_exscan_4096");
 static_assert((KD_THREADS & (KD_THREADS - 1)) == 0, "the key order of the bucket passes needs a power of 2");
 constexpr int KD_BUCKET_MAX = 512;
 
@@ -635,11 +636,13 @@ __device__ __forceinline__ float2 ff_warp_sum8(const float2 (&v)[8], int lane) {
 // arrays: bucket sort, else register-resident radix passes); MODE 1: keys in
 // the global ping-pong
 // buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
-// With Lf != NULL the bin's fit is left to k_kdist_fit: the kernel writes
-// the folded logarithms (L_j + L_{nb-1-j}, L_j - L_{nb-1-j}) for j < nh, as
+// FIT = false: the bin's fit is left to k_kdist_fit; the kernel writes the
+// folded logarithms (L_j + L_{nb-1-j}, L_j - L_{nb-1-j}) for j < nh, as
 // float-float pairs, to Lf[bin * npad + j] (npad = nh rounded up to 32) and
-// no coefficients; else it fits the bin itself from P in global memory.
-template <int MODE>
+// no coefficients.  FIT = true: it fits the bin itself from P in global
+// memory (the allocation-free entry point, which has no room for Lf).  The
+// two are separate instantiations so that each carries only its own code.
+template <int MODE, bool FIT>
 __global__ void __launch_bounds__(KD_THREADS)
     k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
                 const float2 *__restrict__ P, const float2 *__restrict__ lntab, unsigned long long *gA,
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(KD_THREADS)
   }
   __syncthreads();
   const int nh = (nb + 1) >> 1;
-  if (Lf) {
+  if (!FIT) {
     // folded logarithms for k_kdist_fit (the middle point of an odd bin
     // once, in both halves of its pair)
     const int npad = ((nh + 31) >> 5) << 5;
@@ -797,7 +800,7 @@ __global__ void __launch_bounds__(KD_THREADS)
     }
   }
   __syncthreads();
-  if (!Lf && tid < ncheb) {
+  if (FIT && tid < ncheb) {
     float2 s = red[0][tid];
     for (int i = 1; i < KD_WARPS; ++i) s = ff_add(s, red[i][tid]);
     coef[(int64_t)blockIdx.x * ncheb + tid] = (double)s.x + (double)s.y;
@@ -819,52 +822,89 @@ __global__ void __launch_bounds__(KD_THREADS)
 
 // --------------------------------------------------------------- the fit --
 // c = P L for many bins at once: a CTA takes KF_BINS bins (one warp each)
-// and one group of P's column blocks, stages P's columns through shared
-// memory one chunk of KF_COLS at a time and applies each chunk to all its
-// bins, so P is read from L2 once per KF_BINS bins (instead of once per bin);
-// every lane accumulates the ncheb coefficients of its bin over its columns
-// in double-float (dfma_acc), the warp reduces them, and the partial sums of
-// the column groups go to `part` ([group][bin][k]), added in a fixed order by
-// k_kdist_fit_sum.
+// and one group of P's column blocks, and streams them through shared
+// memory in chunks of KF_COLS columns -- the chunk of P and, for each of its
+// bins, the chunk of folded logarithms -- by cp.async, double-buffered so
+// that the next chunk's copies fly while the current one is used.  So P is
+// read from L2 once per KF_BINS bins instead of once per bin.  Every lane
+// accumulates the ncheb coefficients of its bin over its columns in
+// double-float (dfma_acc), the warp reduces them, and the partial sums of
+// the column groups go to `part` ([group][bin][k]), added in a fixed order
+// by k_kdist_fit_sum.
 constexpr int KF_BINS = 8;
 constexpr int KF_THREADS = 32 * KF_BINS;
-constexpr int KF_COLS = 64;  // columns (two 32-column blocks of P) per chunk
+constexpr int KF_COLS = 128;  // columns (four 32-column blocks of P) per chunk
 
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Shared memory of k_kdist_fit: two stages of [P chunk | folded logs].
+size_t kdist_fit_smem(int ncheb) {
+  return 2 * ((size_t)ncheb * KF_COLS * sizeof(float2) + (size_t)KF_BINS * KF_COLS * sizeof(float4));
+}
+
+// NC: a compile-time bound on ncheb (8, 16, 20, 24 or 32), so that no
+// issue slot goes to coefficients beyond it.
+template <int NC>
 __global__ void __launch_bounds__(KF_THREADS)
-    k_kdist_fit(const float4 *__restrict__ Lf, int npad, int nh, int nbins, int ncheb,
-                const float2 *__restrict__ P, int cols_per_group, float2 *__restrict__ part) {
-  __shared__ float2 Pst[NCHEB_MAX * KF_COLS];  // [32-column block][k][32]
+    k_kdist_fit(const float4 *__restrict__ Lf, int npad, int nbins, int ncheb, const float2 *__restrict__ P,
+                int cols_per_group, float2 *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char kf_smem[];
   __shared__ float2 wred[KF_BINS][NCHEB_MAX];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = blockIdx.x;
   const int bin = blockIdx.y * KF_BINS + w;
   const int c0 = g * cols_per_group, c1 = min(npad, c0 + cols_per_group);
-  const float4 *lrow = Lf + (int64_t)min(bin, nbins - 1) * npad;
-  float sh[NCHEB_MAX], sl[NCHEB_MAX];
-#pragma unroll
-  for (int k = 0; k < NCHEB_MAX; ++k) sh[k] = sl[k] = 0.0f;
-  for (int cc = c0; cc < c1; cc += KF_COLS) {
+  // stage st: [P chunk (ncheb x KF_COLS float2) | folded logs (KF_BINS x KF_COLS float4)]
+  const size_t pbytes = (size_t)ncheb * KF_COLS * sizeof(float2);
+  const size_t sbytes = pbytes + (size_t)KF_BINS * KF_COLS * sizeof(float4);
+  auto Pst = [&](int st) { return reinterpret_cast<float2 *>(kf_smem + st * sbytes); };
+  auto Lst = [&](int st) { return reinterpret_cast<float4 *>(kf_smem + st * sbytes + pbytes); };
+  const int b0 = blockIdx.y * KF_BINS;
+  // copies of the chunk at columns cc into stage st (each thread its share)
+  auto issue = [&](int cc, int st) {
     const int ncol = min(KF_COLS, c1 - cc);  // a multiple of 32
-    // the chunk of P: whole 32-column blocks, contiguous in the blocked layout
-    const float2 *src = P + (int64_t)(cc >> 5) * ncheb * 32;
-    for (int e = tid; e < ncol * ncheb; e += KF_THREADS) Pst[e] = src[e];
-    __syncthreads();
+    const float2 *src = P + (int64_t)(cc >> 5) * ncheb * 32;  // whole blocks, contiguous
+    const int np = ncol * ncheb / 2;                          // 16-byte pieces of P
+    for (int e = tid; e < np; e += KF_THREADS) cp_async16(Pst(st) + 2 * e, src + 2 * e);
+    // the folded logs: warp wb copies its bin's row (ncol is a multiple of 32)
+    {
+      const int wb = tid >> 5;
+      const float4 *row = Lf + (int64_t)min(b0 + wb, nbins - 1) * npad + cc;
+      for (int cl = tid & 31; cl < ncol; cl += 32) cp_async16(Lst(st) + wb * KF_COLS + cl, row + cl);
+    }
+  };
+  constexpr int NR = (NC + 7) / 8 * 8;  // accumulators, a multiple of the reduction's 8
+  float sh[NR], sl[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) sh[k] = sl[k] = 0.0f;
+  if (c0 < c1) issue(c0, 0);
+  cp_async_commit();
+  int st = 0;
+  for (int cc = c0; cc < c1; cc += KF_COLS, st ^= 1) {
+    if (cc + KF_COLS < c1) issue(cc + KF_COLS, st ^ 1);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of the current chunk have landed
+    __syncthreads();   // and everyone's
+    const int ncol = min(KF_COLS, c1 - cc);
     if (bin < nbins) {
       for (int b = 0; b < (ncol >> 5); ++b) {
-        const int j = cc + 32 * b + lane;
-        const float4 l = lrow[j];  // zero past nh
+        const float4 l = Lst(st)[w * KF_COLS + 32 * b + lane];  // zero past nh
         const float2 Lp = make_float2(l.x, l.y), Lm = make_float2(l.z, l.w);
-        const float2 *pb = Pst + b * ncheb * 32 + lane;
+        const float2 *pb = Pst(st) + b * ncheb * 32 + lane;
 #pragma unroll
-        for (int k = 0; k < NCHEB_MAX; ++k)
+        for (int k = 0; k < NC; ++k)
           if (k < ncheb) dfma_acc(sh[k], sl[k], pb[k * 32], (k & 1) ? Lm : Lp);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the stage is refilled two chunks on
   }
   // warp sums, eight coefficients at a time (reduce-scatter)
 #pragma unroll
-  for (int k0 = 0; k0 < NCHEB_MAX; k0 += 8) {
+  for (int k0 = 0; k0 < NR; k0 += 8) {
     float2 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -924,16 +964,16 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   float4 *Lf = reinterpret_cast<float4 *>(c->kd_fold);
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
     const size_t smem = (size_t)nb * 16;
-    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     ++c->launches;
-    k_kdist_bin<0><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
-                                                           nullptr, nullptr, coef, mean, kg_out, Lf);
+    k_kdist_bin<0, false><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
+                                                                  nullptr, nullptr, coef, mean, kg_out, Lf);
   } else {
     ++c->launches;
-    k_kdist_bin<1><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
-                                                        c->sort_a, c->sort_b, coef, mean, kg_out, Lf);
+    k_kdist_bin<1, false><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
+                                                               c->sort_a, c->sort_b, coef, mean, kg_out, Lf);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -941,9 +981,14 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   const int groups = fit_groups(c, npad, nbins);
   const int cpg = ((npad / 32 + groups - 1) / groups) * 32;
   float2 *part = reinterpret_cast<float2 *>(c->kd_part);
+  const size_t fsm = kdist_fit_smem(ncheb);
+  auto fit = ncheb <= 8 ? k_kdist_fit<8> : ncheb <= 16 ? k_kdist_fit<16> : ncheb <= 20 ? k_kdist_fit<20>
+           : ncheb <= 24 ? k_kdist_fit<24> : k_kdist_fit<32>;
+  e = cudaFuncSetAttribute(fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  if (e != cudaSuccess) return e;
   ++c->launches;
-  k_kdist_fit<<<dim3(groups, (nbins + KF_BINS - 1) / KF_BINS), KF_THREADS, 0, c->stream>>>(
-      Lf, npad, nh, nbins, ncheb, P, cpg, part);
+  fit<<<dim3(groups, (nbins + KF_BINS - 1) / KF_BINS), KF_THREADS, fsm, c->stream>>>(Lf, npad, nbins, ncheb, P,
+                                                                                     cpg, part);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++c->launches;
@@ -1097,12 +1142,12 @@ extern "C" helk_status helk_kdist_static(const double *kappa, int64_t n, int32_t
                                    reinterpret_cast<float2 *>(ptr + 2 * KDIST_STATIC_PINV),
                                    reinterpret_cast<long long *>(ptr + KDIST_STATIC_TAG));
   if (cudaGetLastError() != cudaSuccess) return HELK_ERR_CUDA;
-  if (cudaFuncSetAttribute(k_kdist_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_kdist_bin<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return HELK_ERR_CUDA;
   }
-  k_kdist_bin<0><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor,
+  k_kdist_bin<0, true><<<nbins, KD_THREADS, smem, st>>>(kappa, (int)nb, ncheb, kappa_floor,
                                                   reinterpret_cast<const float2 *>(ptr),
                                                   reinterpret_cast<const float2 *>(ptr + 2 * KDIST_STATIC_PINV),
                                                   nullptr, nullptr, coeffs, mean, kg_out, nullptr);

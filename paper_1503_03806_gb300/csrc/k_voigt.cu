@@ -30,7 +30,7 @@ namespace helk {
 // interleave); mixed pairs -- those containing a method boundary or the line
 // core -- decide per point.
 enum { CLS_GH1 = 1, CLS_GH3 = 2, CLS_MIXED = 3 };  // 0: the line misses the warp
-constexpr int KAHAN_GROUP = 12;             // lines per compensated partial
+constexpr int KAHAN_GROUP = 16;             // lines per compensated partial
 
 // Whether a core evaluation at (x, y) lies in a cell where the surrogate
 // network was validated (features as in k_mlp.cu).
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   const uint32_t max_seq = (uint32_t)min(
       (unsigned long long)nitems * (unsigned long long)(nlines / LCH + 2) + 2 * F32_STAGES, 0x7FFFFFFFull);
   // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
-  // into part[k] (relative error <= 11 u) and Kahan-adds the partial into
-  // (sum, comp); total relative error < 8e-7.
+  // into part[k] (relative error <= 15 u, all terms positive) and Kahan-adds
+  // the partial into (sum, comp); total relative error < 1e-6.
   float sum[NSLOT], comp[NSLOT], part[NSLOT];
   int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
@@ -612,14 +612,33 @@ __global__ void __launch_bounds__(CORE_BLOCK)
   }
 }
 
+// v 2^E as a double, for a normal float v, from its bits (integer
+// operations only: the conversion and scaling would otherwise be two
+// operations of the FP64 unit, which runs at 1/64 of the FP32 rate here).
+// Exact: the double holds v's sign and 24-bit significand at the shifted
+// exponent.  A subnormal v, or a result outside the double's normal
+// range, takes the FP64 route.
+__device__ __forceinline__ double scaled_to_double(float v, int E) {
+  const unsigned b = __float_as_uint(v);
+  const int ef = (int)((b >> 23) & 0xFF);
+  const int e = ef - 127 + 1023 + E;
+  if (ef == 0 || e <= 0 || e >= 2047) return ldexp((double)v, E);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)e << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFF) << 29)));
+}
+
 // kappa += 2^E weight kcore at the points with a core sum (as k_voigt_f32's
-// flush scales its sums)
+// flush scales its sums); for weight 1 the scaled value is formed on the
+// integer pipe, leaving one FP64 addition a point.
 __global__ void __launch_bounds__(256)
     k_core_add(const float *__restrict__ kcore_all, int ngrid, double weight, double *__restrict__ kappa_all,
                const CondStats *cst) {
   const int cond = blockIdx.y;
   if (cst[cond].core_w1 == 0) return;
-  const double scale = ldexp(weight, cst[cond].scale_exp);
+  const int E = cst[cond].scale_exp;
+  const double scale = ldexp(weight, E);
+  const bool unit = weight == 1.0;
   const float *kcore = kcore_all + (int64_t)cond * ngrid;
   double *kappa = kappa_all + (int64_t)cond * ngrid;
   // four points a thread per pass, their loads issued together
@@ -634,7 +653,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t i = i0 + q * stride;
-      if (v[q] != 0.0f) kappa[i] += scale * (double)v[q];
+      if (v[q] != 0.0f) kappa[i] += unit ? scaled_to_double(v[q], E) : scale * (double)v[q];
     }
   }
 }
