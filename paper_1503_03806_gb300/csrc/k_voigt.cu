@@ -30,7 +30,7 @@ namespace helk {
 // interleave); mixed pairs -- those containing a method boundary or the line
 // core -- decide per point.
 enum { CLS_GH1 = 1, CLS_GH3 = 2, CLS_MIXED = 3 };  // 0: the line misses the warp
-constexpr int KAHAN_GROUP = 16;             // lines per compensated partial
+constexpr int KAHAN_GROUP = 32;             // lines per compensated partial
 
 // Whether a core evaluation at (x, y) lies in a cell where the surrogate
 // network was validated (features as in k_mlp.cu).
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   const uint32_t max_seq = (uint32_t)min(
       (unsigned long long)nitems * (unsigned long long)(nlines / LCH + 2) + 2 * F32_STAGES, 0x7FFFFFFFull);
   // Compensated accumulation: each point sums KAHAN_GROUP lines plainly
-  // into part[k] (relative error <= 15 u, all terms positive) and Kahan-adds
-  // the partial into (sum, comp); total relative error < 1e-6.
+  // into part[k] (relative error <= 31 u, all terms positive) and Kahan-adds
+  // the partial into (sum, comp); total relative error < 2e-6.
   float sum[NSLOT], comp[NSLOT], part[NSLOT];
   int ngroup = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
