@@ -132,11 +132,17 @@ struct Gh3Line {
     c45 = -4.5f * P3h;
     c2 = P3h * fmaf(12.0f, a2_, 4.5f);
   }
-  // part + term, for the point's r2 = u^2 + a^2
-  __device__ __forceinline__ float add(float part, float r2) const {
+  // numerator and denominator of the term, for the point's r2 = u^2 + a^2
+  __device__ __forceinline__ void nd(float r2, float &n, float &d) const {
     const float p = fmaf(r2, r2 - 3.0f, C);
-    const float n = fmaf(r2, fmaf(c3, r2, c45), c2);
-    return fmaf(n, fast_rcp(r2 * p), part);
+    n = fmaf(r2, fmaf(c3, r2, c45), c2);
+    d = r2 * p;
+  }
+  // part + term
+  __device__ __forceinline__ float add(float part, float r2) const {
+    float n, d;
+    nd(r2, n, d);
+    return fmaf(n, fast_rcp(d), part);
   }
 };
 
@@ -497,23 +503,28 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           }
         } else {
           // Per point: GH1 or GH3; core points (r^2 < 100) are left to the
-          // core kernel (k_core_f32).
+          // core kernel (k_core_f32).  Branch-free, so the slots stay
+          // independent chains: the method's numerator and denominator are
+          // selected before one reciprocal (the same operations, in the same
+          // order, as the whole-span loops), and the sum is kept where the
+          // point is outside the window or in the core.
           const int j = __float_as_int(W.q1);
           const float P1 = W.q0;
           const Gh3Line g3(a2, buf[j].P3);
 #pragma unroll
           for (int k = 0; k < NSLOT; ++k) {
             const int i = wbase + lane + 32 * k;
-            if ((unsigned)(i - lo) <= (unsigned)(hi - lo)) {
-              const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
-              const float r2 = fmaf(u, u, a2);
-              if (r2 >= 1.0e6f) {
-                part[k] = fmaf(P1, fast_rcp(r2), part[k]);
-                if (COUNT) cnt[2]++;
-              } else if (r2 >= 100.0f) {
-                part[k] = g3.add(part[k], r2);
-                if (COUNT) cnt[1]++;
-              }
+            const float u = fmaf(d0 + (float)(32 * k), beta, nphi);
+            const float r2 = fmaf(u, u, a2);
+            float n, d;
+            g3.nd(r2, n, d);  // not used (possibly infinite) where GH1 applies
+            const bool gh1 = r2 >= 1.0e6f;
+            const bool use = (unsigned)(i - lo) <= (unsigned)(hi - lo) && r2 >= 100.0f;
+            const float t = fmaf(gh1 ? P1 : n, fast_rcp(gh1 ? r2 : d), part[k]);
+            part[k] = use ? t : part[k];
+            if (COUNT) {
+              cnt[2] += use && gh1;
+              cnt[1] += use && !gh1;
             }
           }
         }
