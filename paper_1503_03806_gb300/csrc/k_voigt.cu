@@ -700,11 +700,12 @@ cudaError_t launch_core_add(helk_ctx *c, int n_cond, const helk_grid &g, const h
 // the number of tiles can be matched to whole waves of resident CTAs (equal
 // tiles finish together, so a partial last wave idles the rest of the GPU);
 // the other entries vary the CTA size (4, 12 warps) and the stage length (64,
-// 256 lines) for the autotuner.
+// 256 lines, the latter also with 10-12 slots) for the autotuner.
 #define HELK_F32_SHAPES(X)                                                                          \
   X(8, 6, 128, 3) X(8, 7, 128, 3) X(8, 8, 128, 3) X(8, 9, 128, 2) X(8, 10, 128, 2) X(8, 11, 128, 2)   \
   X(8, 12, 128, 2) X(8, 13, 128, 2) X(8, 14, 128, 2) X(8, 16, 128, 2) X(8, 8, 64, 3) X(8, 8, 256, 3)  \
-  X(8, 7, 256, 3) X(4, 8, 128, 6) X(4, 9, 128, 4) X(12, 8, 128, 2)
+  X(8, 7, 256, 3) X(4, 8, 128, 6) X(4, 9, 128, 4) X(12, 8, 128, 2) X(8, 10, 256, 2) X(8, 11, 256, 2)  \
+  X(8, 12, 256, 2)
 constexpr int F32_COUNT_CODE = 3;  // the counting variant (statistics): 8 warps, 8 slots, 128 lines
 constexpr int F32_COUNT_NSLOT = 8, F32_COUNT_WARPS = 8, F32_COUNT_LCH = 128;
 
