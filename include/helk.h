@@ -118,7 +118,11 @@ typedef struct {
                            cells to the network (helk_surrogate_*); error
                            <= 1e-4 relative per routed term.  The routed
                            terms are added with atomics, so results are no
-                           longer bitwise reproducible.                    */
+                           longer bitwise reproducible.  0 (the default)
+                           keeps Algorithm 916: on GB300 the network is
+                           slower than the FP32 Algorithm 916 it replaces
+                           (its 192 SiLU activations take more MUFU time
+                           than a whole FP32 evaluation).                  */
 } helk_opts;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream`
