@@ -704,7 +704,13 @@ __global__ void __launch_bounds__(KD_THREADS)
       cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
     S = A;
   } else {
-    S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
+    // bins too large for shared memory: the same bucket sort through the
+    // global ping-pong buffers (about 11 accesses a key against 24 for the
+    // eight radix passes), the radix passes when a bucket is too full
+    if (vmin == vmax || cta_bucket_sort(A, gB + off, nb, hist, wtot, vmin, vmax))
+      S = A;
+    else
+      S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
   }
   // sorted values out, the bin sum, and L_j in place as a split pair
   const unsigned long long kmax = S[nb - 1];

@@ -163,3 +163,12 @@ def test_invalid_arguments(ctx):
         with pytest.raises(helk.HelkError) as e:
             ctx.kdist(k, nbins, ncheb, floor)
         assert e.value.status == helk.HELK_ERR_INVALID_ARG
+
+
+def test_global_path_bucket_and_radix(ctx):
+    # bins of 30000 points (sorted through the global buffers): the bucket
+    # sort, and, with more than 512 equal keys in a bucket, the radix passes
+    k = synth.uniform_kappa(2 * 30000, 31)
+    check_kdist(ctx, k, 2, 20)
+    check_kdist(ctx, _with_zeros(k, 2, 1000), 2, 20, floor=1e-40)
+    check_kdist(ctx, _tied_high_words(3 * 30000, 3, 32), 3, 20)
