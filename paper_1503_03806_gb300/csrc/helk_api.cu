@@ -164,6 +164,7 @@ void helk_destroy(helk_ctx *c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->kcore) cudaFree(c->kcore);
+  if (c->core_blk) cudaFree(c->core_blk);
   for (int st = 0; st < HELK_NSTAGES; ++st)
     for (cudaEvent_t e : c->ev[st]) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
@@ -343,6 +344,8 @@ static helk_status ensure_call_buffers(helk_ctx *c, int n_cond, const helk_opts 
     HELK_TRY(ensure_buf(c, (void **)&c->ckey32, &c->ckey32_cap, std::max<int64_t>(c->nlines, 1) * 4,
                         "line keys"));
     HELK_TRY(ensure_buf(c, (void **)&c->kcore, &c->kcore_cap, ngrid * n_cond * 4, "core sums"));
+    HELK_TRY(ensure_buf(c, (void **)&c->core_blk, &c->core_blk_cap, (int64_t)core_blocks(ngrid) * n_cond * 4,
+                        "core reach"));
     if (!c->side_stream)
       HELK_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking), "core stream"));
     if (!c->fork_ev)
@@ -386,7 +389,11 @@ static helk_status prepare_lines(helk_ctx *c, int n_cond, const CondArgs *single
   if (c->nlines > 0) {
     HELK_TRY(cuda_check(c, launch_lineprep(c, n_cond, single, mass, *cut, *g, o.precision != HELK_PREC_F32_KAHAN),
                         "lineprep"));
-    if (o.precision == HELK_PREC_F32_KAHAN) HELK_TRY(cuda_check(c, launch_pack32(c, n_cond, *g), "pack32"));
+    if (o.precision == HELK_PREC_F32_KAHAN) {
+      HELK_TRY(cuda_check(c, cudaMemsetAsync(c->core_blk, 0, (size_t)core_blocks(g->n) * n_cond * 4, c->stream),
+                          "pack32"));
+      HELK_TRY(cuda_check(c, launch_pack32(c, n_cond, *g), "pack32"));
+    }
   }
   return HELK_OK;
 }
@@ -543,7 +550,9 @@ static std::string batch_key(const helk_ctx *c, int n_cond, double mass, const h
   snprintf(b2, sizeof b2, "|%d%d%d%d%d%d|%p|%p|%p|%p", c->has_E, c->has_gself, c->has_ncoll, c->has_delta,
            c->has_mass, c->has_weight, (const void *)c->cond_host, (const void *)c->cond_dev,
            (const void *)c->cond_order, (const void *)c->core_rng);
-  return std::string(b) + b2;
+  char b3[64];
+  snprintf(b3, sizeof b3, "|%p", (const void *)c->core_blk);
+  return std::string(b) + b2 + b3;
 }
 
 // The per-condition arrays as seen by a chunk of a batch: offset by the

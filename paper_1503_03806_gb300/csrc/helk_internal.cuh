@@ -116,6 +116,13 @@ struct CondStats {
 //                   where the FP32 form's point offsets are no longer exact
 enum { ERRF_TIMEOUT = 1, ERRF_F32_RANGE = 2 };
 
+// FP32 form: grid points per block of the per-block core reach (the largest
+// distance from a line's reference index to a point of its core, over the
+// lines whose reference index lies in the block), which bounds the candidate
+// lines of the core kernel's warps.
+constexpr int CORE_BLK_PTS = 4096;
+__host__ __device__ inline int core_blocks(int64_t ngrid) { return (int)((ngrid + CORE_BLK_PTS - 1) / CORE_BLK_PTS); }
+
 // ---------------------------------------------------------- the context --
 }  // namespace helk
 
@@ -139,6 +146,8 @@ struct helk_ctx {
   helk::LineRec32 *rec32 = nullptr;
   int2 *core_rng = nullptr;  // FP32 form: each line's core points [x, y] (x > y: none)
   int64_t core_cap = 0;
+  int *core_blk = nullptr;   // FP32 form: 1 + core reach per block of CORE_BLK_PTS points, per condition
+  int64_t core_blk_cap = 0;
   double *ckey = nullptr;
   int64_t ckey_cap = 0;
   int32_t *ckey32 = nullptr;  // FP32 form: ckey clamped to the int32 range (order kept), for integer searches

@@ -407,7 +407,8 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // relative precision near the line centre.
 __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu, int64_t ngrid,
                          const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
-                         int2 *__restrict__ core_all, int32_t *__restrict__ ckey32, int *err_flags) {
+                         int2 *__restrict__ core_all, int32_t *__restrict__ ckey32, int *err_flags,
+                         int *__restrict__ core_blk_all, int nblk) {
   const int cond = blockIdx.y;
   const LineRec64 *r64 = r64_all + (int64_t)cond * n;
   LineRec32 *r32 = r32_all + (int64_t)cond * n;
@@ -480,8 +481,13 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
         const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
         if (clo <= chi) {
           const double w = fmax(key - clo, chi - key);
-          cw1 = max(cw1, (int)fmin(w + 1.0, 2.0e9));
+          const int w1 = (int)fmin(w + 1.0, 2.0e9);
+          cw1 = max(cw1, w1);
           core = make_int2((int)clo, (int)chi);
+          // the reach of the lines whose reference index lies in each block
+          // of CORE_BLK_PTS grid points (the core kernel's candidate window)
+          const int blk = (int)fmin(fmax(floor(key / (double)CORE_BLK_PTS), 0.0), (double)(nblk - 1));
+          atomicMax(&core_blk_all[(int64_t)cond * nblk + blk], w1);
         }
       }
     }
@@ -497,7 +503,8 @@ cudaError_t launch_pack32(helk_ctx *c, int n_cond, const helk_grid &g) {
   dim3 grid(line_blocks(c, n, n_cond), n_cond);
   ++c->launches;
   k_pack32<<<grid, 256, 0, c->stream>>>(n, c->rec64, g.nu_min, g.dnu, g.n, c->ckey, c->cstats, c->rec32,
-                                        c->core_rng, c->ckey32, &c->stats->err_flags);
+                                        c->core_rng, c->ckey32, &c->stats->err_flags, c->core_blk,
+                                        core_blocks(g.n));
   return cudaGetLastError();
 }
 

@@ -89,6 +89,23 @@ __device__ __forceinline__ float fast_rcp(float x) {
   return r;
 }
 
+// v 2^E as a double, for a normal float v, from its bits (integer
+// operations only: the conversion and scaling would otherwise be two
+// operations of the FP64 unit, which runs at 1/64 of the FP32 rate here).
+// Exact: the double holds v's sign and 24-bit significand at the shifted
+// exponent; zero stays (signed) zero.  A subnormal v, or a result outside
+// the double's normal range, takes the FP64 route.
+__device__ __forceinline__ double scaled_to_double(float v, int E) {
+  const unsigned b = __float_as_uint(v);
+  if ((b & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)((unsigned long long)(b >> 31) << 63));
+  const int ef = (int)((b >> 23) & 0xFF);
+  const int e = ef - 127 + 1023 + E;
+  if (ef == 0 || e <= 0 || e >= 2047) return ldexp((double)v, E);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)e << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFF) << 29)));
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   const float y = v - c;
   const float t = s + y;
@@ -352,13 +369,19 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       if (cur >= 0) {  // the previous tile is complete: write it
         const int cond = cond_order[cur / ntiles];
         double *kappa = kappa_all + (int64_t)cond * ngrid;
-        const double scale = ldexp(weight, cst[cond].scale_exp);
+        const int E = cst[cond].scale_exp;
+        const double scale = ldexp(weight, E);
+        const bool unit = weight == 1.0;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
           kahan_add(sum[k], comp[k], part[k]);
           const int i = wbase + lane + 32 * k;
           if (i < ngrid) {
-            const double v = scale * ((double)sum[k] - (double)comp[k]);
+            // 2^E (sum - comp): for weight 1 the two scaled values are formed on
+            // the integer pipe (exact) and one FP64 subtraction rounds, the
+            // same result as scaling the FP64 difference
+            const double v = unit ? scaled_to_double(sum[k], E) - scaled_to_double(comp[k], E)
+                                  : scale * ((double)sum[k] - (double)comp[k]);
             kappa[i] = accumulate ? kappa[i] + v : v;
           }
         }
@@ -565,7 +588,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(CORE_BLOCK)
     k_core_f32(const LineRec32 *__restrict__ rec_all, const int2 *__restrict__ core_all, int64_t nlines,
                const int32_t *__restrict__ ckey, int ngrid, float *__restrict__ kcore_all, CondStats *cst,
-               SurrQueue *sq) {
+               SurrQueue *sq, const int *__restrict__ core_blk_all) {
   // per warp: the series weights of the line being evaluated
   __shared__ float s_w[CORE_BLOCK / 32][32];
   const int cond = blockIdx.y;
@@ -577,7 +600,22 @@ __global__ void __launch_bounds__(CORE_BLOCK)
   const int lane = threadIdx.x & 31;
   float *w = s_w[threadIdx.x >> 5];
   const int64_t B = min(A + 32, (int64_t)ngrid);
-  const int64_t W = cw1 - 1;  // integer searches (FP64 is the scarce unit here)
+  // The candidate window: the condition's largest core reach, or, when that
+  // is below a block, the largest reach of the lines whose reference index
+  // lies in this block or its two neighbours (no line from a farther block
+  // reaches the warp); the core reach grows with the line centre, so the
+  // low-wavenumber warps scan far fewer lines.
+  int64_t W = cw1 - 1;
+  if (W < CORE_BLK_PTS - 32) {
+    const int nblk = core_blocks(ngrid);
+    const int b = (int)(A / CORE_BLK_PTS);
+    const int *cb = core_blk_all + (int64_t)cond * nblk;
+    int r = cb[b];
+    if (b > 0) r = max(r, cb[b - 1]);
+    if (b + 1 < nblk) r = max(r, cb[b + 1]);
+    W = r - 1;  // -1: no line near this block has a core
+  }
+  // integer searches (FP64 is the scarce unit here)
   const int64_t first = warp_search(ckey, 0, nlines, A - W, false);
   const int64_t last = warp_search(ckey, first, nlines, B - 1 + W, true);
   const LineRec32 *rec = rec_all + (int64_t)cond * nlines;
@@ -623,22 +661,6 @@ __global__ void __launch_bounds__(CORE_BLOCK)
   }
 }
 
-// v 2^E as a double, for a normal float v, from its bits (integer
-// operations only: the conversion and scaling would otherwise be two
-// operations of the FP64 unit, which runs at 1/64 of the FP32 rate here).
-// Exact: the double holds v's sign and 24-bit significand at the shifted
-// exponent.  A subnormal v, or a result outside the double's normal
-// range, takes the FP64 route.
-__device__ __forceinline__ double scaled_to_double(float v, int E) {
-  const unsigned b = __float_as_uint(v);
-  const int ef = (int)((b >> 23) & 0xFF);
-  const int e = ef - 127 + 1023 + E;
-  if (ef == 0 || e <= 0 || e >= 2047) return ldexp((double)v, E);
-  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
-                                          ((unsigned long long)e << 52) |
-                                          ((unsigned long long)(b & 0x7FFFFF) << 29)));
-}
-
 // kappa += 2^E weight kcore at the points with a core sum (as k_voigt_f32's
 // flush scales its sums); for weight 1 the scaled value is formed on the
 // integer pipe, leaving one FP64 addition a point.
@@ -676,10 +698,10 @@ cudaError_t launch_voigt_core(helk_ctx *c, int n_cond, const helk_grid &g, const
   ++c->launches;
   if (o.count_regions)
     k_core_f32<true><<<grid, CORE_BLOCK, 0, c->side_stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey32,
-                                                               (int)g.n, c->kcore, c->cstats, sq);
+                                                               (int)g.n, c->kcore, c->cstats, sq, c->core_blk);
   else
     k_core_f32<false><<<grid, CORE_BLOCK, 0, c->side_stream>>>(c->rec32, c->core_rng, c->nlines, c->ckey32,
-                                                                (int)g.n, c->kcore, c->cstats, sq);
+                                                                (int)g.n, c->kcore, c->cstats, sq, c->core_blk);
   return cudaGetLastError();
 }
 
