@@ -120,7 +120,7 @@ enum { ERRF_TIMEOUT = 1, ERRF_F32_RANGE = 2 };
 // distance from a line's reference index to a point of its core, over the
 // lines whose reference index lies in the block), which bounds the candidate
 // lines of the core kernel's warps.
-constexpr int CORE_BLK_PTS = 4096;
+constexpr int CORE_BLK_PTS = 4096;  // 2^12 (k_pack32 takes the block by a shift)
 __host__ __device__ inline int core_blocks(int64_t ngrid) { return (int)((ngrid + CORE_BLK_PTS - 1) / CORE_BLK_PTS); }
 
 // ---------------------------------------------------------- the context --

@@ -468,6 +468,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     // point from the reference index bounds the core kernel's candidate
     // search.
     int2 core = make_int2(1, 0);
+    int line_w1 = 0;  // 1 + the line's core reach, 0: no core
     if (q.a2 < 100.0f && q.ihi >= q.ilo && q.beta > 0.0f) {
       const float reach = clamped ? 10.001f - fabsf(q.phi_k) : 10.001f + fabsf(q.phi_k);
       if (reach > 0.0f) {
@@ -481,17 +482,23 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
         const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
         if (clo <= chi) {
           const double w = fmax(key - clo, chi - key);
-          const int w1 = (int)fmin(w + 1.0, 2.0e9);
-          cw1 = max(cw1, w1);
+          line_w1 = (int)fmin(w + 1.0, 2.0e9);
+          cw1 = max(cw1, line_w1);
           core = make_int2((int)clo, (int)chi);
-          // the reach of the lines whose reference index lies in each block
-          // of CORE_BLK_PTS grid points (the core kernel's candidate window)
-          const int blk = (int)fmin(fmax(floor(key / (double)CORE_BLK_PTS), 0.0), (double)(nblk - 1));
-          atomicMax(&core_blk_all[(int64_t)cond * nblk + blk], w1);
         }
       }
     }
     core_all[(int64_t)cond * n + l] = core;
+    // The reach of the lines whose reference index lies in each block of
+    // CORE_BLK_PTS grid points (the core kernel's candidate window): the
+    // list is ordered by the index, so the lanes of a warp mostly share a
+    // block and one atomic per block and warp suffices.
+    const int k32 = (int)fmin(fmax(key, -2147483647.0), 2147483647.0);
+    const int blk = min(max(k32 >> 12, 0), nblk - 1);  // CORE_BLK_PTS = 2^12
+    const unsigned peers = __match_any_sync(__activemask(), blk);
+    const int wblk = __reduce_max_sync(peers, line_w1);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && wblk > 0)
+      atomicMax(&core_blk_all[(int64_t)cond * nblk + blk], wblk);
   }
   for (int o = 16; o > 0; o >>= 1) cw1 = max(cw1, __shfl_down_sync(0xffffffffu, cw1, o));
   if ((threadIdx.x & 31) == 0 && cw1 > 0) atomicMax(&cst->core_w1, cw1);
