@@ -168,3 +168,23 @@ def test_lines_just_outside_the_grid(ctx, cut):
     assert ev == evo and rego[0] > 0
     assert np.abs(reg[:3] - rego).sum() <= max(4, 1e-4 * evo)
     check_binned(k, ko, 10, "lines just outside the grid, %s" % cut[0])
+
+
+def test_range_of_the_fp32_form_is_reported(ctx):
+    # A Doppler core wider than 2^23 grid points (here a 1e-9 cm^-1 grid step):
+    # the FP32 form's point offsets are exact only within 2^24 points, so the
+    # call is reported as unsupported at the next synchronisation (no fault),
+    # once; the FP64 form takes the same call, and the context stays usable.
+    from paper_1503_03806_gb300 import helk
+    lines = {"nu0": np.array([1000.0 + 5e-7]), "S0": np.array([1e-20]), "gamma_air": np.array([0.05])}
+    case = Case(1500.0, 1e-6, 18.0, (1000.0, 1e-9, 1000), ("abs", 1.0))
+    ctx.upload(lines)
+    case.gpu(ctx, precision=helk.HELK_PREC_F32_KAHAN)
+    with pytest.raises(helk.HelkError) as e:
+        ctx.sync()
+    assert e.value.status == helk.HELK_ERR_UNSUPPORTED
+    ctx.sync()  # reported once
+    k = case.gpu(ctx).cpu().numpy()  # FP64 form
+    ctx.sync()
+    ko, _, _ = oracle.opacity(lines, case.oracle_cond())
+    assert np.max(np.abs(k - ko) / ko) <= 1e-9
