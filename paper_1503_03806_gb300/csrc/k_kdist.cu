@@ -430,6 +430,30 @@ __device__ void cta_radix_sort_reg(unsigned long long *A, int nb, uint32_t *hist
   }
 }
 
+// The bin sum in 128-bit unsigned fixed point (lo, hi), exactly: a value
+// m 2^(e - 1075) (m < 2^53, e the biased exponent, 1 for subnormals) is
+// added as m 2^(e - emax + fxb), where emax is the largest value's exponent
+// and fxb = 74 - ceil(log2 N_b), so N_b terms stay below 2^127.  Terms of a
+// negative exponent are truncated (each below 2^-(fxb + 52) of the largest
+// value).  Integer operations only.
+__device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long long &hi, unsigned long long kb,
+                                       int emax, int fxb) {
+  const int e = (int)(kb >> 52);
+  const unsigned long long m = (kb & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int sh = max(e, 1) - emax + fxb;
+  unsigned long long tl = 0, th = 0;
+  if (sh >= 64) {
+    th = m << (sh - 64);
+  } else if (sh > 0) {
+    tl = m << sh;
+    th = m >> (64 - sh);
+  } else if (sh > -53) {
+    tl = m >> -sh;
+  }
+  lo += tl;
+  hi += th + (lo < tl);
+}
+
 // Bucket sort of a bin held in shared memory: the keys' range [kmin, kmax]
 // is cut into KD_NBUCKET buckets of equal width in key space (the key bits
 // are monotone in the value and close to its logarithm), the keys are
@@ -447,8 +471,22 @@ constexpr int KD_BUCKET_MAX = 512;
 
 __device__ __forceinline__ int hpad(int b) { return b + (b >> 4); }  // block_exscan_4096's layout
 
+// What the last step of a bucket sort can do with each key at its place
+// besides storing it: with LOGS, it stores L = ln max(k, floor) (as the
+// float-float pair log_ff gives) in place of the key, writes the key to the
+// sorted output, if any, and adds it to the thread's 128-bit bin sum, so
+// that no separate pass over the sorted keys is needed.
+struct KeyLogs {
+  const float2 *lnc, *invc;
+  unsigned long long floor_bits;
+  double *kg;  // sorted output of the bin, or NULL
+  int emax, fxb;
+};
+
+template <bool LOGS>
 __device__ bool cta_bucket_sort(unsigned long long *A, unsigned long long *B, int nb, uint32_t *hist,
-                                uint32_t *wtot, unsigned long long kmin, unsigned long long kmax) {
+                                uint32_t *wtot, unsigned long long kmin, unsigned long long kmax,
+                                const KeyLogs &kl, unsigned long long &fx_lo, unsigned long long &fx_hi) {
   const int tid = threadIdx.x;
   const int sh = max(0, 64 - __clzll((long long)(kmax - kmin)) - 12);  // (kmax - kmin) >> sh < 4096
   for (int i = tid; i < KD_HIST; i += KD_THREADS) hist[i] = 0;
@@ -483,7 +521,14 @@ __device__ bool cta_bucket_sort(unsigned long long *A, unsigned long long *B, in
       const unsigned long long x = B[i];
       r += (x < k) || (x == k && i < j);
     }
-    A[r] = k;
+    if (LOGS) {
+      if (kl.kg) kl.kg[r] = __longlong_as_double((long long)k);
+      fx_add(fx_lo, fx_hi, k, kl.emax, kl.fxb);
+      // non-negative doubles order as their bit patterns: max(k, floor) on the bits
+      reinterpret_cast<float2 *>(A)[r] = log_ff(k > kl.floor_bits ? k : kl.floor_bits, kl.lnc, kl.invc);
+    } else {
+      A[r] = k;
+    }
   }
   __syncthreads();
   return true;
@@ -572,30 +617,6 @@ __device__ __forceinline__ void dfma_acc(float &sh, float &sl, float2 P, float2 
   const float err = (sh - (t - z)) + (p - z);
   sh = t;
   sl += err + (e + fmaf(P.x, L.y, P.y * L.x));
-}
-
-// The bin sum in 128-bit unsigned fixed point (lo, hi), exactly: a value
-// m 2^(e - 1075) (m < 2^53, e the biased exponent, 1 for subnormals) is
-// added as m 2^(e - emax + fxb), where emax is the largest value's exponent
-// and fxb = 74 - ceil(log2 N_b), so N_b terms stay below 2^127.  Terms of a
-// negative exponent are truncated (each below 2^-(fxb + 52) of the largest
-// value).  Integer operations only.
-__device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long long &hi, unsigned long long kb,
-                                       int emax, int fxb) {
-  const int e = (int)(kb >> 52);
-  const unsigned long long m = (kb & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-  const int sh = max(e, 1) - emax + fxb;
-  unsigned long long tl = 0, th = 0;
-  if (sh >= 64) {
-    th = m << (sh - 64);
-  } else if (sh > 0) {
-    tl = m << sh;
-    th = m >> (64 - sh);
-  } else if (sh > -53) {
-    tl = m >> -sh;
-  }
-  lo += tl;
-  hi += th + (lo < tl);
 }
 
 __device__ __forceinline__ void fx_warp_sum(unsigned long long &lo, unsigned long long &hi) {
@@ -697,34 +718,40 @@ __global__ void __launch_bounds__(KD_THREADS)
     vmin = min(vmin, red_min[i]);
     vmax = max(vmax, red_max[i]);
   }
+  // the bin sum (128-bit fixed point, relative to the largest key) and the
+  // logarithms' arguments
+  const unsigned long long kmax = vmax;
+  const int emax = max((int)(kmax >> 52), 1);
+  const int fxb = 74 - (nb > 1 ? 32 - __clz(nb - 1) : 0);
+  unsigned long long fx_lo = 0, fx_hi = 0;
+  const unsigned long long floor_bits = (unsigned long long)__double_as_longlong(kappa_floor);
+  const KeyLogs kl{s_lnc, s_invc, floor_bits, kg_out ? kg_out + off : nullptr, emax, fxb};
+  bool logged = false;  // the bucket sort's last step took the logarithms
   unsigned long long *S;
   if (MODE == 0) {
     // the second key array of the bucket sort follows A in shared memory
-    if (vmin != vmax && !cta_bucket_sort(A, A + nb, nb, hist, wtot, vmin, vmax))
-      cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
+    if (vmin != vmax) {
+      logged = cta_bucket_sort<true>(A, A + nb, nb, hist, wtot, vmin, vmax, kl, fx_lo, fx_hi);
+      if (!logged) cta_sort_bin(A, kappa + off, nb, hist, wtot, vand ^ vor);
+    }
     S = A;
   } else {
     // bins too large for shared memory: the same bucket sort through the
     // global ping-pong buffers (about 11 accesses a key against 24 for the
     // eight radix passes), the radix passes when a bucket is too full
-    if (vmin == vmax || cta_bucket_sort(A, gB + off, nb, hist, wtot, vmin, vmax))
+    if (vmin == vmax || cta_bucket_sort<false>(A, gB + off, nb, hist, wtot, vmin, vmax, kl, fx_lo, fx_hi))
       S = A;
     else
       S = cta_radix_sort(A, gB + off, nb, hist, wtot, vand ^ vor);
   }
   // sorted values out, the bin sum, and L_j in place as a split pair
-  const unsigned long long kmax = S[nb - 1];
-  const int emax = max((int)(kmax >> 52), 1);
-  const int fxb = 74 - (nb > 1 ? 32 - __clz(nb - 1) : 0);
-  unsigned long long fx_lo = 0, fx_hi = 0;
   float2 *Ls = reinterpret_cast<float2 *>(S);
-  const unsigned long long floor_bits = (unsigned long long)__double_as_longlong(kappa_floor);
-  __syncthreads();  // every thread has read kmax before L_j overwrites the keys
+  __syncthreads();
   // four points a thread per pass: their keys are read before any L_j is
   // written in place, so the four logarithms run side by side (the integer
   // bin sum does not depend on the order)
   constexpr int LU = 4;
-  for (int j0 = tid; j0 < nb; j0 += LU * KD_THREADS) {
+  for (int j0 = logged ? nb : tid; j0 < nb; j0 += LU * KD_THREADS) {
     unsigned long long kq[LU];
 #pragma unroll
     for (int q = 0; q < LU; ++q) {
