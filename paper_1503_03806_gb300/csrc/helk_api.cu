@@ -148,7 +148,7 @@ void helk_destroy(helk_ctx *c) {
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
                   c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->ckey32, c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
-                  c->mean_dev, c->tmp, c->kd_fold, c->kd_part};
+                  c->mean_dev, c->tmp, c->kd_fold, c->kd_part, c->kd_done};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (c->stats_host) cudaFreeHost(c->stats_host);
@@ -750,7 +750,8 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
     c->pinv_nb = nb;
     c->pinv_ncheb = ncheb;
   }
-  if (nb > kdist_smem_max_points(c)) {
+  {  // the global sort buffers: the bins too large for shared memory, and the
+     // radix passes of a bin whose bucket sort gives up
     if (n * 8 > c->sort_cap) {
       HELK_TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "kdist"));
       if (c->sort_a) cudaFree(c->sort_a);
@@ -764,6 +765,10 @@ helk_status helk_kdist(helk_ctx *c, const double *kappa, int64_t n, int32_t nbin
   }
   HELK_TRY(ensure_buf(c, &c->kd_fold, &c->kd_fold_cap, kdist_fold_bytes(n, nbins), "kdist scratch"));
   HELK_TRY(ensure_buf(c, &c->kd_part, &c->kd_part_cap, kdist_part_bytes(c, n, nbins), "kdist scratch"));
+  if (kdist_done_bytes(nbins) > c->kd_done_cap) {
+    HELK_TRY(ensure_buf(c, &c->kd_done, &c->kd_done_cap, kdist_done_bytes(nbins), "kdist scratch"));
+    HELK_TRY(cuda_check(c, cudaMemsetAsync(c->kd_done, 0, (size_t)c->kd_done_cap, c->stream), "kdist scratch"));
+  }
   double *cdst = coeffs, *mdst = mean;
   if (out_on_host) {
     HELK_TRY(ensure_buf(c, (void **)&c->coef_dev, &c->coef_cap, (int64_t)nbins * ncheb * 8, "kdist out"));

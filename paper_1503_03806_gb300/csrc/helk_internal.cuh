@@ -187,8 +187,10 @@ struct helk_ctx {
   double *pinv = nullptr;  // pseudo-inverse of the Chebyshev design matrix
   int64_t pinv_cap = 0, pinv_nb = 0;
   int pinv_ncheb = 0;
-  void *kd_fold = nullptr, *kd_part = nullptr;  // fit stage: folded logarithms, partial sums
-  int64_t kd_fold_cap = 0, kd_part_cap = 0;
+  // fit stage: logarithm pairs, partial sums, per-row counts of finished
+  // CTAs (zero between calls)
+  void *kd_fold = nullptr, *kd_part = nullptr, *kd_done = nullptr;
+  int64_t kd_fold_cap = 0, kd_part_cap = 0, kd_done_cap = 0;
   double *coef_dev = nullptr, *mean_dev = nullptr;
   int64_t coef_cap = 0, mean_cap = 0;
   // Voigt surrogate network (k_mlp.cu): FP32 parameters, Adam moments,
@@ -365,6 +367,7 @@ int64_t kdist_smem_max_points(helk_ctx *c);
 // scratch of the fit stage: folded logarithms, per-group partial sums
 int64_t kdist_fold_bytes(int64_t n, int nbins);
 int64_t kdist_part_bytes(helk_ctx *c, int64_t n, int nbins);
+int64_t kdist_done_bytes(int nbins);
 // k_mlp.cu
 constexpr int MLP_NPARAMS_H = 8577;
 cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const double *x, const double *y,

@@ -659,10 +659,13 @@ __device__ __forceinline__ float2 ff_warp_sum8(const float2 (&v)[8], int lane) {
 // buffers gA, gB.  P holds the pseudo-inverse as split pairs [k][j].
 // FIT = false: the bin's fit is left to k_kdist_fit; the kernel writes the
 // folded logarithms (L_j + L_{nb-1-j}, L_j - L_{nb-1-j}) for j < nh, as
-// float-float pairs, to Lf[bin * npad + j] (npad = nh rounded up to 32) and
-// no coefficients.  FIT = true: it fits the bin itself from P in global
-// memory (the allocation-free entry point, which has no room for Lf).  The
-// two are separate instantiations so that each carries only its own code.
+// float-float pairs, to Lf[bin * npad + j] (npad = nh rounded up to 32,
+// zero past nh), and no coefficients.
+// FIT = true: it fits the bin itself from P in global memory (the
+// allocation-free entry point, which has no room for Lf).  The two are
+// separate instantiations so that each carries only its own code.  Bins
+// that fit in shared memory once take k_kdist_rank instead of MODE 0 with
+// FIT = false.
 template <int MODE, bool FIT>
 __global__ void __launch_bounds__(KD_THREADS)
     k_kdist_bin(const double *__restrict__ kappa, int nb, int ncheb, double kappa_floor,
@@ -853,17 +856,299 @@ __global__ void __launch_bounds__(KD_THREADS)
   }
 }
 
+// ---------------------------------------------- bins in shared memory --
+// The per-bin stage (FIT = false) for bins whose keys fit in shared memory
+// once: 8 B a point for the key, 2 B for its place.  The keys are read from
+// kappa three times (the range from HBM, then the bucket counts and the
+// scatter from L2), so that shared memory holds only the keys in bucket
+// order, the bucket counters are 16-bit, and two CTAs of a 10^4-point bin
+// share an SM (the barrier-separated phases of one overlap the other's).
+// Each key's rank is its bucket's start plus the keys of the bucket that
+// are smaller, or equal and earlier (as in cta_bucket_sort); the rank pass
+// records, per sorted place, the key's position in B, and a last pass takes
+// the places in order, each with its mirror nb-1-j, and writes their outputs
+// with coalesced stores (pair_out): the sorted values, their terms of the
+// bin sum, and the folded logarithms of L = ln max(k, floor).  A bucket of more than KD_BUCKET_MAX
+// keys is ranked by position when all its keys are equal (a run of zeros or
+// of one floor value: equal keys are equal values); any other such bucket
+// sends the bin to the radix passes through the global buffers gA, gB.
+struct BinOut {
+  const float2 *lnc, *invc;
+  unsigned long long floor_bits;
+  double *kg;  // the bin's sorted output, or NULL
+  float4 *X;   // the bin's row of folded logarithms
+  int nb, emax, fxb;
+};
+
+// The outputs of sorted place j < nh and of its mirror nb-1-j, from their
+// keys ka and kb: the sorted values, their terms of the bin sum, and the
+// folded logarithms (L_j + L_{nb-1-j}, L_j - L_{nb-1-j}) as float-float
+// pairs in X[j] (the middle point of an odd bin: L_j in both).  The two
+// logarithms run side by side.
+__device__ __forceinline__ void pair_out(const BinOut &o, int j, unsigned long long ka, unsigned long long kb,
+                                         unsigned long long &fx_lo, unsigned long long &fx_hi) {
+  const int m = o.nb - 1 - j;
+  // non-negative doubles order as their bit patterns: max(k, floor) on the bits
+  const float2 La = log_ff(ka > o.floor_bits ? ka : o.floor_bits, o.lnc, o.invc);
+  const float2 Lb = log_ff(kb > o.floor_bits ? kb : o.floor_bits, o.lnc, o.invc);
+  if (o.kg) o.kg[j] = __longlong_as_double((long long)ka);
+  fx_add(fx_lo, fx_hi, ka, o.emax, o.fxb);
+  float2 Lp = La, Lm = La;
+  if (m != j) {
+    if (o.kg) o.kg[m] = __longlong_as_double((long long)kb);
+    fx_add(fx_lo, fx_hi, kb, o.emax, o.fxb);
+    Lp = ff_add(La, Lb);
+    Lm = ff_add(La, make_float2(-Lb.x, -Lb.y));
+  }
+  o.X[j] = make_float4(Lp.x, Lp.y, Lm.x, Lm.y);
+}
+
+// The bucket counters of k_kdist_rank as 16-bit halves of 32-bit words
+// (bins of fewer than 2^16 points): bucket b in half b & 1 of word b >> 1,
+// the words padded by one every 16 (fewer bank conflicts in the scan).
+constexpr int KR_HWORDS = KD_NBUCKET / 2 + KD_NBUCKET / 32;
+__device__ __forceinline__ int hw_idx(int wi) { return wi + (wi >> 4); }
+__device__ __forceinline__ uint32_t hw_get(const uint32_t *hw, int b) {
+  return (hw[hw_idx(b >> 1)] >> ((b & 1) << 4)) & 0xFFFFu;
+}
+// returns the bucket's counter before the increment
+__device__ __forceinline__ uint32_t hw_inc(uint32_t *hw, int b) {
+  const int s = (b & 1) << 4;
+  return (atomicAdd(&hw[hw_idx(b >> 1)], 1u << s) >> s) & 0xFFFFu;
+}
+
+// Exclusive scan of the KD_NBUCKET packed counters in bucket order, in place
+// (every partial sum below 2^16).
+__device__ void block_exscan_4096_u16(uint32_t *hw, uint32_t *wtot) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t loc[4];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    loc[i] = hw[hw_idx(tid * 4 + i)];
+    s += (loc[i] & 0xFFFFu) + (loc[i] >> 16);
+  }
+  uint32_t v = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wtot[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < KD_WARPS ? wtot[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane < KD_WARPS) wtot[lane] = x;
+  }
+  __syncthreads();
+  uint32_t run = v - s + (w > 0 ? wtot[w - 1] : 0u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = run;
+    run += loc[i] & 0xFFFFu;
+    hw[hw_idx(tid * 4 + i)] = lo | (run << 16);
+    run += loc[i] >> 16;
+  }
+  __syncthreads();
+}
+
+// A key's place in the bin from its bucket in B (bucket ends in hw): the
+// bucket's start plus its keys that are smaller, or equal and earlier in B;
+// a bucket of more than KD_BUCKET_MAX keys holds one value (checked by the
+// caller), so its keys take their places in B.
+__device__ __forceinline__ int bucket_rank(const unsigned long long *B, const uint32_t *hw, unsigned long long k,
+                                           int p, unsigned long long vmin, int sh) {
+  const int b = (int)((k - vmin) >> sh);
+  const int lo = b > 0 ? (int)hw_get(hw, b - 1) : 0, hi = (int)hw_get(hw, b);
+  if (hi - lo > KD_BUCKET_MAX) return p;
+  int r = lo;
+  for (int i = lo; i < hi; ++i) {
+    const unsigned long long x = B[i];
+    r += (x < k) || (x == k && i < p);
+  }
+  return r;
+}
+
+constexpr int KR_UNROLL = 4;  // keys a thread has in flight in the passes over kappa
+
+__global__ void __launch_bounds__(KD_THREADS, 2)
+    k_kdist_rank(const double *__restrict__ kappa, int nb, int npad, double kappa_floor,
+                 const float2 *__restrict__ lntab, unsigned long long *gA, unsigned long long *gB,
+                 double *__restrict__ mean, double *__restrict__ kg_out, float4 *__restrict__ X) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint32_t hw[KR_HWORDS];
+  __shared__ uint32_t wtot[32];
+  __shared__ unsigned long long red[4][KD_WARPS];
+  __shared__ unsigned long long red_fx[KD_WARPS][2];
+  __shared__ float2 s_lnc[128], s_invc[128];
+  // keys in bucket order, then each sorted place's position in B (16 bits)
+  unsigned long long *B = reinterpret_cast<unsigned long long *>(dsm);
+  uint16_t *Q = reinterpret_cast<uint16_t *>(dsm + (size_t)nb * 8);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t off = (int64_t)blockIdx.x * nb;
+  const unsigned long long *K = reinterpret_cast<const unsigned long long *>(kappa + off);
+  // the keys' range (and the bits in which they differ, for the radix passes)
+  unsigned long long vand = ~0ull, vor = 0ull, vmin = ~0ull, vmax = 0ull;
+  for (int j0 = tid; j0 < nb; j0 += KR_UNROLL * KD_THREADS) {
+    unsigned long long kq[KR_UNROLL];
+#pragma unroll
+    for (int q = 0; q < KR_UNROLL; ++q) {
+      const int j = j0 + q * KD_THREADS;
+      kq[q] = K[j < nb ? j : j0];  // a repeat of a key changes none of the four
+    }
+#pragma unroll
+    for (int q = 0; q < KR_UNROLL; ++q) {
+      vand &= kq[q];
+      vor |= kq[q];
+      vmin = min(vmin, kq[q]);
+      vmax = max(vmax, kq[q]);
+    }
+  }
+  if (tid < KD_LNTAB) {  // ln c_j and 1/c_j as FP32 (high, low) pairs
+    const float2 t = lntab[tid];
+    if (tid < 128)
+      s_lnc[tid] = t;
+    else
+      s_invc[tid - 128] = t;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vand &= __shfl_down_sync(0xffffffffu, vand, o);
+    vor |= __shfl_down_sync(0xffffffffu, vor, o);
+    vmin = min(vmin, __shfl_down_sync(0xffffffffu, vmin, o));
+    vmax = max(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+  }
+  if (lane == 0) {
+    red[0][w] = vand;
+    red[1][w] = vor;
+    red[2][w] = vmin;
+    red[3][w] = vmax;
+  }
+  const int nh = (nb + 1) >> 1;
+  float4 *Xb = X + (int64_t)blockIdx.x * npad;
+  for (int jj = nh + tid; jj < npad; jj += KD_THREADS) Xb[jj] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  __syncthreads();
+  // (the bits of the AND, the OR and the largest key stay in `red` for the
+  // radix passes and the mean)
+  vmin = ~0ull;
+  vmax = 0ull;
+  for (int i = 0; i < KD_WARPS; ++i) {
+    vmin = min(vmin, red[2][i]);
+    vmax = max(vmax, red[3][i]);
+  }
+  const int emax = max((int)(vmax >> 52), 1);
+  const int fxb = 74 - (nb > 1 ? 32 - __clz(nb - 1) : 0);
+  const BinOut o{s_lnc, s_invc, (unsigned long long)__double_as_longlong(kappa_floor),
+                 kg_out ? kg_out + off : nullptr, Xb, nb, emax, fxb};
+  unsigned long long fx_lo = 0, fx_hi = 0;
+  bool bucketed = true;  // CTA-uniform: false sends the bin to the radix passes
+  if (vmin == vmax) {
+    for (int j = tid; j < nh; j += KD_THREADS) pair_out(o, j, vmin, vmin, fx_lo, fx_hi);
+  } else {
+    const int sh = max(0, 64 - __clzll((long long)(vmax - vmin)) - 12);  // (vmax - vmin) >> sh < 4096
+    for (int i = tid; i < KR_HWORDS; i += KD_THREADS) hw[i] = 0;
+    __syncthreads();
+    // neighbouring grid points have close values: the lanes of a warp take
+    // keys 97 apart, so that their atomics mostly go to different counters
+    const int pt = (tid * 97) & (KD_THREADS - 1);
+    for (int j0 = pt; j0 < nb; j0 += KR_UNROLL * KD_THREADS) {
+      unsigned long long kq[KR_UNROLL];
+#pragma unroll
+      for (int q = 0; q < KR_UNROLL; ++q) {
+        const int j = j0 + q * KD_THREADS;
+        kq[q] = j < nb ? K[j] : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < KR_UNROLL; ++q)
+        if (j0 + q * KD_THREADS < nb) hw_inc(hw, (int)((kq[q] - vmin) >> sh));
+    }
+    __syncthreads();
+    uint32_t mx = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mx = max(mx, hw_get(hw, tid * 8 + i));
+    const bool big = __syncthreads_or(mx > (uint32_t)KD_BUCKET_MAX);
+    block_exscan_4096_u16(hw, wtot);  // bucket starts
+    for (int j0 = pt; j0 < nb; j0 += KR_UNROLL * KD_THREADS) {
+      unsigned long long kq[KR_UNROLL];
+#pragma unroll
+      for (int q = 0; q < KR_UNROLL; ++q) {
+        const int j = j0 + q * KD_THREADS;
+        kq[q] = j < nb ? K[j] : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < KR_UNROLL; ++q)
+        if (j0 + q * KD_THREADS < nb) B[hw_inc(hw, (int)((kq[q] - vmin) >> sh))] = kq[q];
+    }
+    __syncthreads();  // hw now holds each bucket's end
+    if (big) {
+      // is every bucket over KD_BUCKET_MAX keys a run of one value?
+      bool mixed = false;
+      for (int p = tid; p < nb; p += KD_THREADS) {
+        const unsigned long long k = B[p];
+        const int b = (int)((k - vmin) >> sh);
+        const int lo = b > 0 ? (int)hw_get(hw, b - 1) : 0, hi = (int)hw_get(hw, b);
+        mixed |= hi - lo > KD_BUCKET_MAX && k != B[lo];
+      }
+      bucketed = !__syncthreads_or(mixed);
+    }
+    if (bucketed) {
+      for (int p = tid; p < nb; p += KD_THREADS) Q[bucket_rank(B, hw, B[p], p, vmin, sh)] = (uint16_t)p;
+      __syncthreads();
+      for (int j = tid; j < nh; j += KD_THREADS) pair_out(o, j, B[Q[j]], B[Q[nb - 1 - j]], fx_lo, fx_hi);
+    }
+  }
+  if (!bucketed) {
+    unsigned long long *A = gA + off;
+    for (int j = tid; j < nb; j += KD_THREADS) A[j] = K[j];
+    vand = ~0ull;
+    vor = 0ull;
+    for (int i = 0; i < KD_WARPS; ++i) {
+      vand &= red[0][i];
+      vor |= red[1][i];
+    }
+    __syncthreads();
+    // the radix passes' counters in the (now unused) key array
+    const unsigned long long *S =
+        cta_radix_sort(A, gB + off, nb, reinterpret_cast<uint32_t *>(dsm), wtot, vand ^ vor);
+    for (int j = tid; j < nh; j += KD_THREADS) pair_out(o, j, S[j], S[nb - 1 - j], fx_lo, fx_hi);
+  }
+  fx_warp_sum(fx_lo, fx_hi);
+  if (lane == 0) {
+    red_fx[w][0] = fx_lo;
+    red_fx[w][1] = fx_hi;
+  }
+  __syncthreads();
+  if (tid == 0 && mean) {
+    unsigned long long lo = 0, hi = 0, kmax = 0;
+    for (int i = 0; i < KD_WARPS; ++i) {
+      lo += red_fx[i][0];
+      hi += red_fx[i][1] + (lo < red_fx[i][0]);
+      kmax = max(kmax, red[3][i]);
+    }
+    double m;
+    if ((kmax >> 52) >= 0x7FF)  // infinite or NaN largest value (or a negative one)
+      m = (kmax >> 63) ? __longlong_as_double(0x7FF8000000000000ll) : __longlong_as_double((long long)kmax);
+    else
+      m = ldexp(fma((double)hi, 0x1p64, (double)lo), max((int)(kmax >> 52), 1) - 1075 - fxb) / (double)nb;
+    mean[blockIdx.x] = m;
+  }
+}
+
 // --------------------------------------------------------------- the fit --
 // c = P L for many bins at once: a CTA takes KF_BINS bins (one warp each)
 // and one group of P's column blocks, and streams them through shared
 // memory in chunks of KF_COLS columns -- the chunk of P and, for each of its
-// bins, the chunk of folded logarithms -- by cp.async, double-buffered so
-// that the next chunk's copies fly while the current one is used.  So P is
-// read from L2 once per KF_BINS bins instead of once per bin.  Every lane
-// accumulates the ncheb coefficients of its bin over its columns in
-// double-float (dfma_acc), the warp reduces them, and the partial sums of
-// the column groups go to `part` ([group][bin][k]), added in a fixed order
-// by k_kdist_fit_sum.
+// bins, the chunk of folded logarithms (L_j + L_{nb-1-j} for the even
+// coefficients, L_j - L_{nb-1-j} for the odd ones) -- by cp.async,
+// double-buffered so that the next chunk's copies fly while the current one
+// is used.  So P is read from L2 once per KF_BINS bins instead of once per
+// bin.  Every lane accumulates the ncheb coefficients of its bin over its
+// columns in double-float (dfma_acc), the warp reduces them, and the partial sums of the column groups go to `part`
+// ([group][bin][k]).  The last CTA of a row of bins to finish (counted in
+// `done`, which it sets back to zero) adds the groups' partial sums in group
+// order, so the result does not depend on which CTA finishes last.
 constexpr int KF_BINS = 8;
 constexpr int KF_THREADS = 32 * KF_BINS;
 constexpr int KF_COLS = 128;  // columns (four 32-column blocks of P) per chunk
@@ -884,9 +1169,11 @@ size_t kdist_fit_smem(int ncheb) {
 template <int NC>
 __global__ void __launch_bounds__(KF_THREADS)
     k_kdist_fit(const float4 *__restrict__ Lf, int npad, int nbins, int ncheb, const float2 *__restrict__ P,
-                int cols_per_group, float2 *__restrict__ part) {
+                int cols_per_group, float2 *__restrict__ part, unsigned int *__restrict__ done,
+                double *__restrict__ coef) {
   extern __shared__ __align__(16) unsigned char kf_smem[];
   __shared__ float2 wred[KF_BINS][NCHEB_MAX];
+  __shared__ bool s_last;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = blockIdx.x;
   const int bin = blockIdx.y * KF_BINS + w;
@@ -951,16 +1238,22 @@ __global__ void __launch_bounds__(KF_THREADS)
   __syncwarp();
   if (bin < nbins && lane < ncheb)
     part[((int64_t)g * nbins + bin) * ncheb + lane] = wred[w][lane];
-}
-
-// coef[b][k] = sum over the column groups of the partial sums, in group order
-__global__ void k_kdist_fit_sum(const float2 *__restrict__ part, int ngroups, int nbins, int ncheb,
-                                double *__restrict__ coef) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (int64_t)nbins * ncheb) return;
-  float2 s = part[e];
-  for (int g = 1; g < ngroups; ++g) s = ff_add(s, part[(int64_t)g * nbins * ncheb + e]);
-  coef[e] = (double)s.x + (double)s.y;
+  __threadfence();  // the partial sums are visible device-wide before the count
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned int prev = atomicAdd(&done[blockIdx.y], 1u);
+    s_last = prev == gridDim.x - 1;
+    if (s_last) done[blockIdx.y] = 0;  // every group has counted: ready for the next call
+  }
+  __syncthreads();
+  if (s_last && bin < nbins && lane < ncheb) {
+    __threadfence();
+    const float2 *pe = part + (int64_t)bin * ncheb + lane;
+    const int64_t gs = (int64_t)nbins * ncheb;
+    float2 s = __ldcg(pe);
+    for (int gg = 1; gg < (int)gridDim.x; ++gg) s = ff_add(s, __ldcg(pe + gg * gs));
+    coef[(int64_t)bin * ncheb + lane] = (double)s.x + (double)s.y;
+  }
 }
 
 int64_t kdist_fold_bytes(int64_t n, int nbins) {
@@ -982,11 +1275,24 @@ int64_t kdist_part_bytes(helk_ctx *c, int64_t n, int nbins) {
   return (int64_t)fit_groups(c, (int)npad, nbins) * nbins * NCHEB_MAX * 8;
 }
 
+int64_t kdist_done_bytes(int nbins) { return (int64_t)((nbins + KF_BINS - 1) / KF_BINS) * 4; }
+
 int64_t kdist_smem_max_points(helk_ctx *c) {
-  // two shared-memory key arrays (16 B a point) beside ~26 KB of static smem
-  const int64_t fixed = 26 * 1024;
-  const int64_t avail = (int64_t)c->max_smem_optin - fixed;
-  return std::min<int64_t>(KD_REG_MAX, avail > 0 ? avail / 16 : 0);
+  // k_kdist_rank: the keys (8 B a point) and their sorted places (2 B)
+  // beside its static shared memory
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_kdist_rank) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int64_t avail = (int64_t)c->max_smem_optin - (int64_t)fa.sharedSizeBytes - 16;
+  return std::min<int64_t>(65535, avail > 0 ? avail / 10 : 0);  // 16-bit counters and places
+}
+
+// k_kdist_rank's dynamic shared memory: the keys and their 16-bit places,
+// at least the radix passes' counters (which reuse it).
+static size_t kdist_rank_smem(int nb) {
+  return std::max<size_t>(((size_t)nb * 10 + 15) / 16 * 16, (size_t)KD_HIST * 4);
 }
 
 cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int nbins, int ncheb,
@@ -995,14 +1301,14 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   const float2 *P = reinterpret_cast<const float2 *>(c->pinv);
   const float2 *lntab = pinv_lntab(c, nb, ncheb);
   float4 *Lf = reinterpret_cast<float4 *>(c->kd_fold);
+  const int nh = (nb + 1) / 2, npad = (nh + 31) / 32 * 32;
   if ((int64_t)nb <= kdist_smem_max_points(c)) {
-    const size_t smem = (size_t)nb * 16;
-    cudaError_t e = cudaFuncSetAttribute(k_kdist_bin<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = kdist_rank_smem(nb);
+    cudaError_t e = cudaFuncSetAttribute(k_kdist_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ++c->launches;
-    k_kdist_bin<0, false><<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
-                                                                  nullptr, nullptr, coef, mean, kg_out, Lf);
+    k_kdist_rank<<<nbins, KD_THREADS, smem, c->stream>>>(kappa, nb, npad, kappa_floor, lntab, c->sort_a,
+                                                         c->sort_b, mean, kg_out, Lf);
   } else {
     ++c->launches;
     k_kdist_bin<1, false><<<nbins, KD_THREADS, 0, c->stream>>>(kappa, nb, ncheb, kappa_floor, P, lntab,
@@ -1010,7 +1316,6 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nh = (nb + 1) / 2, npad = (nh + 31) / 32 * 32;
   const int groups = fit_groups(c, npad, nbins);
   const int cpg = ((npad / 32 + groups - 1) / groups) * 32;
   float2 *part = reinterpret_cast<float2 *>(c->kd_part);
@@ -1020,13 +1325,8 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
   e = cudaFuncSetAttribute(fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
   if (e != cudaSuccess) return e;
   ++c->launches;
-  fit<<<dim3(groups, (nbins + KF_BINS - 1) / KF_BINS), KF_THREADS, fsm, c->stream>>>(Lf, npad, nbins, ncheb, P,
-                                                                                     cpg, part);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  ++c->launches;
-  const int64_t ne = (int64_t)nbins * ncheb;
-  k_kdist_fit_sum<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(part, groups, nbins, ncheb, coef);
+  fit<<<dim3(groups, (nbins + KF_BINS - 1) / KF_BINS), KF_THREADS, fsm, c->stream>>>(
+      Lf, npad, nbins, ncheb, P, cpg, part, reinterpret_cast<unsigned int *>(c->kd_done), coef);
   return cudaGetLastError();
 }
 
@@ -1121,6 +1421,7 @@ cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double
 // 2 x 12288 x 32 x 8 B = 6 MiB, held by every device that loads the library
 // until the process exits.
 constexpr int64_t KDIST_STATIC_NB_MAX = 12288;
+static_assert(KDIST_STATIC_NB_MAX <= KD_REG_MAX, "the static path's bins fit the register radix passes");
 constexpr int64_t KDIST_STATIC_PINV = KDIST_STATIC_NB_MAX * NCHEB_MAX;
 constexpr int64_t KDIST_STATIC_TAG = 2 * KDIST_STATIC_PINV + KD_LNTAB;  // offset of the size tag
 static __device__ __align__(256) double g_kdist_scratch[KDIST_STATIC_TAG + 2];

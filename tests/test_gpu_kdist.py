@@ -1,8 +1,10 @@
 """GPU parity of the k-distribution stage (Sec. 2.2, 2.6).
 
 Sorted values: bit-exact against the oracle's library sort on identical
-input, on both sort paths of a shared-memory bin (bucket sort; radix passes
-when a bucket is crowded, e.g. by many equal values).  Chebyshev coefficients: the GPU applies the pseudo-inverse of the
+input, on every sort path of a bin: the bucket sort (a crowded bucket of one
+value, e.g. a run of zeros, ranked by position; one crowded by distinct
+values sends the bin to radix passes), for bins in shared memory and for
+bins in the global buffers.  Chebyshev coefficients: the GPU applies the pseudo-inverse of the
 design matrix shared by all bins (one Householder QR per bin size), the
 oracle runs a Householder QR per bin; both are backward stable and the basis
 is well conditioned at the workloads' bin sizes (cond(A) ~ 5), so the
@@ -89,33 +91,60 @@ def _tied_high_words(n, group, seed):
 
 def _with_zeros(k, nbins, nzero):
     """The same opacities with the first nzero points of every bin set to 0:
-    more than 512 equal keys fill one bucket of the bucket sort, so the bin
-    takes the radix-sort path instead."""
+    more than 512 equal keys fill one bucket of the bucket sort (ranked by
+    position in a shared-memory bin; the radix passes for a bin in the
+    global buffers)."""
     k = k.copy().reshape(nbins, -1)
     k[:, :nzero] = 0.0
     return k.reshape(-1)
 
 
+def _with_crowd(k, nbins, ncrowd, seed):
+    """The same opacities with ncrowd points of every bin replaced by
+    distinct values within 1e-9 of each other (and of 1e-20), in random
+    places: more than 512 different keys in one bucket, so the bin takes
+    the radix passes."""
+    rng = np.random.default_rng(seed)
+    k = k.copy().reshape(nbins, -1)
+    for b in range(nbins):
+        at = rng.choice(k.shape[1], ncrowd, replace=False)
+        k[b, at] = 1e-20 * (1.0 + 1e-9 * rng.random(ncrowd))
+    return k.reshape(-1)
+
+
 def test_high_word_ties_short_runs(ctx):
     # runs of 2..5 keys equal in the high word: in one bucket of the bucket
-    # sort; on the radix path (zeros added) sorted by the low word after the
-    # high-word passes
+    # sort; beside a run of zeros; on the radix passes (a crowded bucket)
     for group in (2, 3, 5):
         k = _tied_high_words(4 * 9000, group, 20 + group)
         check_kdist(ctx, k, 4, 20)
         check_kdist(ctx, _with_zeros(k, 4, 600), 4, 20, floor=1e-40)
+        check_kdist(ctx, _with_crowd(k, 4, 700, group), 4, 20)
 
 
 def test_high_word_ties_long_runs(ctx):
-    # runs longer than one thread sorts on the radix path: the bin is sorted
-    # again by all eight bytes (also a long run of zeros beside an unsorted
-    # short one); runs of 200 in one bucket of the bucket sort
+    # runs of 200 in one bucket of the bucket sort; the same beside a long
+    # run of zeros, and on the radix passes
     k = _tied_high_words(3 * 8000, 200, 31)
     check_kdist(ctx, k, 3, 20)
     check_kdist(ctx, _with_zeros(k, 3, 600), 3, 20, floor=1e-40)
+    check_kdist(ctx, _with_crowd(k, 3, 600, 31), 3, 20)
     k = _tied_high_words(2 * 6000, 2, 32)
     k[:2000] = 0.0
     check_kdist(ctx, k, 2, 20, floor=1e-40)
+
+
+def test_crowded_bucket_takes_the_radix_passes(ctx):
+    # more than 512 distinct keys in one bucket (with and without a run of
+    # zeros in another), bins of the workloads' size and a ragged one
+    for nbins, nb in [(3, 10000), (2, 12345), (5, 1031)]:
+        k = _with_crowd(synth.uniform_kappa(nbins * nb, nb), nbins, 520 if nb < 2000 else 1500, nb)
+        check_kdist(ctx, k, nbins, 20)
+        check_kdist(ctx, _with_zeros(k, nbins, 513), nbins, 20, floor=1e-40)
+    # every bucket crowded but one value each: ranked by position
+    k = np.repeat(synth.uniform_kappa(8, 5), 1000)
+    np.random.default_rng(6).shuffle(k)
+    check_kdist(ctx, k, 2, 20)
 
 
 def test_constant_bin_skips_all_passes(ctx):
