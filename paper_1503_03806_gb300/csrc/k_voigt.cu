@@ -163,6 +163,31 @@ struct Gh3Line {
   }
 };
 
+// The same term far from the line centre as a series in t = 1/r2:
+//   n / (r2 p) = t (c3 + c45 t + c2 t^2) / (1 - 3 t + C t^2)
+//              = t (g0 + g1 t + g2 t^2 + g3 t^3 + ...),
+//   g0 = 3 P3h, g1 = 4.5 P3h, g2 = (11.25 - 6 a^2) P3h, g3 = (23.625 - 45 a^2) P3h
+// (the product of the numerator's coefficients with those of 1/(1 - 3t +
+// C t^2), e_0 = 1, e_1 = 3, e_k = 3 e_{k-1} - C e_{k-2}).  Truncated after g2,
+// on r2 >= R_s with R_s >= 1000 and R_s^3 >= 1.25^3 5e7 (7.875 + 15 a^2)
+// (>= 1.25^3 5e7 |g3/g0|), the relative truncation error is below 1.1e-8 for
+// every a (checked in FP64 on a grid of a^2 in [0, 1e6) and r2 in [R_s, 1e6)),
+// under the FP32 rounding of either form: one reciprocal and three FMAs
+// instead of five FP32 operations and one reciprocal.
+struct Gh3Series {
+  float g0, g1, g2;
+  __device__ __forceinline__ explicit Gh3Series(float a2, float P3) {
+    const float P3h = 2.0f * P3;
+    g0 = 3.0f * P3h;
+    g1 = 4.5f * P3h;
+    g2 = P3h * fmaf(-6.0f, a2, 11.25f);
+  }
+  // does the series hold on a span whose smallest r2 is r2near?
+  static __device__ __forceinline__ bool holds(float r2near, float a2) {
+    return r2near >= 1000.0f && r2near * r2near * r2near >= 9.765625e7f * fmaf(15.0f, a2, 7.875f);
+  }
+};
+
 // ---- FP32 line pipeline: a ring of F32_STAGES chunks of candidate lines,
 // filled by 1-D bulk copies that complete on the stage's mbarrier, with no
 // CTA-wide barrier in the main loop.  Every warp consumes the chunk stream in
@@ -244,19 +269,26 @@ __device__ void f32_drain(F32Pipe &P, int *flags) {
 // and read by the whole warp with three broadcast loads: the kind of the
 // (line, warp) pair, the covered points, the point offset, and the method's
 // constants.
-//   Whole-span lines (one method, GH1 or GH3, on every point of the warp's
-//   span, the line centre outside the span): u is stepped from the span edge
+//   Whole-span lines (one method on every point of the warp's span: GH1, or
+//   GH3 by its expansion in 1/r^2 (Gh3Series) where that holds on the whole
+//   span, r^2 >= R_s; the line centre outside the span): u is stepped from the span edge
 //   nearest the centre, u_k = fma(k - k_b, 32 beta, u_b), one FMA a slot (the
 //   step product is exact, so each u_k is rounded once and |u_b| <= |u_k|
 //   bounds its error by one ulp of u_k); d0 = (float)(base point - c) of lane
 //   0, k_b = 0 (kind *_FWD, centre at or before the span) or NSLOT - 1
 //   (*_BWD, centre at or after it).
-//   The rest (partial cover, a method boundary, the core, or the centre
-//   inside the span): d0 = (float)(wbase - c) and u = (d0 + lane + 32 k) beta
+//   The rest (partial cover, a method boundary, the core, the centre inside
+//   the span, or GH3 nearer the centre than R_s, where the term is formed
+//   exactly): d0 = (float)(wbase - c) and u = (d0 + lane + 32 k) beta
 //   - phi with d0 + lane + 32 k exact, so every point's method (and whether
 //   it is a core point, left to the core kernel) is decided on the same
 //   correctly rounded u as in k_core_f32.
-enum { KIND_MISS = 0, KIND_GH1_FWD = 1, KIND_GH1_BWD = 2, KIND_GH3_FWD = 3, KIND_GH3_BWD = 4, KIND_REST = 5 };
+//   The series covers most of the GH3 region; the GH3 spans nearer the
+//   centre run as the rest rather than in a whole-span loop of their own
+//   (with one loop kind fewer the main loop's code stays within the
+//   instruction caches: 0.743 against 0.763 ms a medium step).
+enum { KIND_MISS = 0, KIND_GH1_FWD = 1, KIND_GH1_BWD = 2, KIND_GH3S_FWD = 3, KIND_GH3S_BWD = 4, KIND_REST = 5 };
+constexpr int NKIND = 5;  // kinds after KIND_MISS
 
 struct __align__(16) WarpLine {
   int kind;          // KIND_*
@@ -264,12 +296,12 @@ struct __align__(16) WarpLine {
   int lo, hi;        // covered points (grid indices; KIND_REST)
   float d0;          // point offset of lane 0 at the base slot (see above)
   float beta, nphi, a2;
-  float q0, q1, q2, q3;  // GH1: P1; GH3: C, c3, c45, c2 (Gh3Line); rest: P1
+  float q0, q1, q2, q3;  // GH1: P1; GH3S: g0, g1, g2 (Gh3Series); rest: P1, or GH3's C, c3, c45, c2 (Gh3Line)
 };
 
 // Whole-span lines [t, t1) of one kind: GH1 (4 instructions an evaluation)
-// or GH3 (9), u stepped from the base slot.
-template <int NSLOT, bool FWD, bool GH3>
+// or GH3 by its series (6), u stepped from the base slot.
+template <int NSLOT, bool FWD, bool GH3S>
 __device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, float lanef, int &ngroup,
                                            float (&sum)[NSLOT], float (&comp)[NSLOT], float (&part)[NSLOT]) {
   while (t < t1) {
@@ -280,12 +312,13 @@ __device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, fl
       const float beta = W.beta, a2 = W.a2;
       const float ub = fmaf(W.d0 + lanef, beta, W.nphi);  // u at the base slot
       const float h = 32.0f * beta;                        // u step between slots (exact)
-      if (GH3) {
-        const Gh3Line g3(a2, W.q0, W.q1, W.q2, W.q3);
+      if (GH3S) {
+        const float g0 = W.q0, g1 = W.q1, g2 = W.q2;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
           const float u = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
-          part[k] = g3.add(part[k], fmaf(u, u, a2));
+          const float t = fast_rcp(fmaf(u, u, a2));
+          part[k] = fmaf(t, fmaf(fmaf(g2, t, g1), t, g0), part[k]);
         }
       } else {
         const float P1 = W.q0;
@@ -416,7 +449,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     WarpLine *wl = s_wl[threadIdx.x >> 5];
     const float lanef = (float)lane;
     for (int m0 = 0; m0 < cnum; m0 += 32) {
-    int nk[5];  // first record of each kind after KIND_GH1_FWD, in kind order
+    int nk[NKIND];  // first record of each kind after KIND_GH1_FWD, in kind order
     {
       const int j = m0 + lane;
       WarpLine r;
@@ -442,15 +475,21 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           r.beta = beta;
           r.nphi = nphi;
           r.a2 = a2;
-          if (full && cls != CLS_MIXED && (dlo >= 0 || dhi <= 0)) {
+          const bool series = cls == CLS_GH3 && Gh3Series::holds(r2near, a2);
+          if (full && (cls == CLS_GH1 || series) && (dlo >= 0 || dhi <= 0)) {
             const bool fwd = dlo >= 0;
-            r.kind = (cls == CLS_GH1 ? KIND_GH1_FWD : KIND_GH3_FWD) + (fwd ? 0 : 1);
+            r.kind = (cls == CLS_GH1 ? KIND_GH1_FWD : KIND_GH3S_FWD) + (fwd ? 0 : 1);
             r.d0 = (float)(fwd ? dlo : dhi - 31);  // lane 0 at slot 0 or NSLOT - 1
           } else {
             r.kind = KIND_REST;
             r.d0 = (float)(wbase - c);
           }
-          if (cls == CLS_GH3) {
+          if (series && r.kind != KIND_REST) {
+            const Gh3Series gs(a2, L.P3);
+            r.q0 = gs.g0;
+            r.q1 = gs.g1;
+            r.q2 = gs.g2;
+          } else if (cls == CLS_GH3) {
             const Gh3Line g3(a2, L.P3);
             r.q0 = g3.C;
             r.q1 = g3.c3;
@@ -463,13 +502,13 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       }
       // records ordered by kind (lines that miss the warp dropped), each
       // kind then runs its own class-free loop
-      unsigned b[5];
+      unsigned b[NKIND];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) b[q] = __ballot_sync(0xffffffffu, r.kind == q + 1);
+      for (int q = 0; q < NKIND; ++q) b[q] = __ballot_sync(0xffffffffu, r.kind == q + 1);
       const unsigned lt = (1u << lane) - 1u;
       int pos = 0, run = 0;
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
+      for (int q = 0; q < NKIND; ++q) {
         if (r.kind == q + 1) pos = run + __popc(b[q] & lt);
         run += __popc(b[q]);
         nk[q] = run;
