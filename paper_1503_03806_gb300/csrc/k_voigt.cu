@@ -317,8 +317,8 @@ __device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, fl
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
           const float u = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
-          const float t = fast_rcp(fmaf(u, u, a2));
-          part[k] = fmaf(t, fmaf(fmaf(g2, t, g1), t, g0), part[k]);
+          const float rr = fast_rcp(fmaf(u, u, a2));  // t = 1/r^2 of the series
+          part[k] = fmaf(rr, fmaf(fmaf(g2, rr, g1), rr, g0), part[k]);
         }
       } else {
         const float P1 = W.q0;
