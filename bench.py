@@ -108,7 +108,7 @@ def kdist_hbm(ms, n, peaks):
     peak = peaks.get("hbm_gbs")
     return {"bytes_per_launch": 8 * n, "achieved": gbs, "unit": "GB/s", "peak": peak,
             "frac": gbs / peak if peak else None,
-            "note": "latency-bound per-bin sort and fit, one CTA per bin; not HBM-bound at 1e4-point bins"}
+            "note": "latency-bound per-bin sort (one 512-thread CTA per bin, two per SM) and fit; not HBM-bound at 1e4-point bins"}
 
 
 def measured_peaks():
