@@ -614,8 +614,9 @@ def leg_transmission(ctx, w, T, P, mass, cut, grid, prec):
         torch.cuda.synchronize()
         out[name + "_ms"] = a.elapsed_time(b) / 3
     out["what"] = ("T_b(m) for %d bins x 1000 column masses: direct = midpoint rule over the %d sorted "
-                   "values of each bin (FP64 exp), fit = midpoint rule over 1000 points of the resampled "
-                   "k(g)" % (nbins, grid[2] // nbins))
+                   "values of each bin, fit = midpoint rule over 1000 points of the resampled k(g); "
+                   "e^{-k_0 m} factored out, terms below e^-87 of it skipped, the rest by a float-float "
+                   "exponential on the FP32 pipe" % (nbins, grid[2] // nbins))
     return out
 
 

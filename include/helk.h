@@ -382,7 +382,17 @@ helk_status helk_peak_probe(helk_ctx *ctx, int32_t kind, double *ops_per_s,
  *   coeffs (device, nbins*ncheb) or NULL: fit[b*nm + i] by the midpoint rule
  *     on ng points of the resampled k(g) = exp(sum_k c_k T_k(2g - 1)).
  * m: host array of nm column masses (cm^2/molecule units inverse to kappa),
- * finite and >= 0.  direct, fit: device arrays of nbins*nm doubles. */
+ * finite and >= 0.  direct, fit: device arrays of nbins*nm doubles.
+ * Arithmetic: the bin's smallest term e^{-k_0 m} in FP64 is factored out;
+ * the others, e^{-(k_j - k_0) m}, are left out below e^-87 of it and
+ * otherwise evaluated as float-float pairs (relative error ~5e-15 a term),
+ * the differences k_j - k_0 formed in FP64.  `sorted` must hold each bin's
+ * values in ascending order (as kg_out does) for the terms past e^-87 to be
+ * found by a search; a bin that is not sorted, or holds a negative or
+ * non-finite value, is summed plainly in FP64.  Each result agrees with the
+ * FP64 sum to ~1e-13 relative (the sum of the fit's points also carries the
+ * FP64 rounding of k(g), ~1e-14 relative, times k m).  Uses context scratch
+ * of 8 B per sorted value. */
 helk_status helk_transmission(helk_ctx *ctx, int32_t nbins, int64_t nb,
                               const double *sorted, const double *coeffs,
                               int32_t ncheb, int32_t ng, int32_t nm,

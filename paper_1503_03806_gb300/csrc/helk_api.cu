@@ -148,7 +148,7 @@ void helk_destroy(helk_ctx *c) {
   void *bufs[] = {c->nu0,  c->S0,     c->El,    c->gair,   c->gself,  c->ncoll,
                   c->delta, c->lmass, c->lweight, c->rec64, c->rec32, c->core_rng, c->ckey, c->ckey32, c->tile_lo, c->tile_hi,
                   c->stats, c->kappa, c->sort_a, c->sort_b, c->pinv,  c->coef_dev,
-                  c->mean_dev, c->tmp, c->kd_fold, c->kd_part, c->kd_done};
+                  c->mean_dev, c->tmp, c->kd_fold, c->kd_part, c->kd_done, c->tr_pairs, c->tr_bins};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (c->stats_host) cudaFreeHost(c->stats_host);
@@ -806,6 +806,10 @@ helk_status helk_transmission(helk_ctx *c, int32_t nbins, int64_t nb, const doub
     if (!(is_fin(m[i]) && m[i] >= 0.0)) return set_err(c, HELK_ERR_INVALID_ARG, "transmission: m must be finite, >= 0");
   HELK_TRY(bind_device(c));
   HELK_TRY(ensure_buf(c, (void **)&c->mass_col, &c->mass_col_cap, (int64_t)nm * 8, "transmission"));
+  if (sorted) {
+    HELK_TRY(ensure_buf(c, &c->tr_pairs, &c->tr_pairs_cap, (int64_t)trans_pair_bytes(nbins, nb), "transmission"));
+    HELK_TRY(ensure_buf(c, &c->tr_bins, &c->tr_bins_cap, (int64_t)trans_bin_bytes(nbins), "transmission"));
+  }
   HELK_TRY(cuda_check(c, cudaMemcpyAsync(c->mass_col, m, (size_t)nm * 8, cudaMemcpyHostToDevice, c->stream),
                       "transmission"));
   HELK_TRY(cuda_check(c, launch_transmission(c, nbins, nb, sorted, coeffs, ncheb, ng, nm, c->mass_col, direct, fit),

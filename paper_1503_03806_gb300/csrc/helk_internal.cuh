@@ -208,6 +208,9 @@ struct helk_ctx {
   // column masses of helk_transmission
   double *mass_col = nullptr;
   int64_t mass_col_cap = 0;
+  // transmission: the bins' differences as scaled pairs, per-bin constants
+  void *tr_pairs = nullptr, *tr_bins = nullptr;
+  int64_t tr_pairs_cap = 0, tr_bins_cap = 0;
   // generic upload scratch
   void *tmp = nullptr;
   int64_t tmp_cap = 0;
@@ -368,6 +371,8 @@ int64_t kdist_smem_max_points(helk_ctx *c);
 int64_t kdist_fold_bytes(int64_t n, int nbins);
 int64_t kdist_part_bytes(helk_ctx *c, int64_t n, int nbins);
 int64_t kdist_done_bytes(int nbins);
+size_t trans_pair_bytes(int nbins, int64_t nb);
+size_t trans_bin_bytes(int nbins);
 // k_mlp.cu
 constexpr int MLP_NPARAMS_H = 8577;
 cudaError_t launch_mlp_eval(helk_ctx *c, const float *params, int64_t n, const double *x, const double *y,

@@ -1333,34 +1333,356 @@ cudaError_t launch_kdist_bins(helk_ctx *c, const double *kappa, int64_t n, int n
 // ---------------------------------------------------------- transmission --
 // T_b(m) = int_0^1 exp(-k(g) m) dg per bin b and column mass m (Sec. 2.1):
 // from the sorted values by the midpoint rule on g_j = (j + 1/2)/N_b, and
-// from the Chebyshev fit by the midpoint rule on ng points.  One CTA per
-// (bin, block of column masses); FP64.
+// from the Chebyshev fit by the midpoint rule on ng points.
+//
+// The smallest value k_0 of a bin is factored out: T = e^{-k_0 m} S / N,
+// S = sum_j e^{-d_j}, d_j = (k_j - k_0) m >= 0, so S lies in [1, N] and each
+// term in (0, 1].  Terms with d_j >= 87 are below 2^-125 of S and left out
+// (for sorted values: every term from the first such j on, found by a binary
+// search); the rest are evaluated on the FP32 pipe as float-float pairs:
+// k_j - k_0 is formed once per point in FP64 and kept as a pair D_j scaled
+// by the bin's 2^-F (F the exponent of the largest difference), d_j = D_j M
+// with M = m 2^F, and e^{-d} by a table-driven exponential (Tang 1989):
+// d = (n/256) ln 2 - r with |r| <= ln2/512, e^{-d} = 2^{-n/256} e^r,
+// 2^{-j/256} from a 256-entry table of pairs and e^r = 1 + r + (r^2/2)(1 +
+// r/3 + r^2/12), the bracket's small part in FP32 (relative error of a term
+// ~5e-15, set by the table's pairs).  Differences below 2^(F-100),
+// whose pairs would lose precision, take FP64 exp; equal values add 1 each.
+// One FP64 exponential per (bin, m) for e^{-k_0 m}.  Bins whose values are
+// not sorted, finite and non-negative take the plain FP64 sum.
 constexpr int TR_THREADS = 256;
+constexpr double TR_DMAX = 87.0;  // e^-87 < 2^-125
 
-__global__ void __launch_bounds__(TR_THREADS)
-    k_trans_direct(const double *__restrict__ sorted, int64_t nb, int nm, const double *__restrict__ m,
-                   double *__restrict__ out) {
-  __shared__ double red[TR_THREADS / 32];
-  const int b = blockIdx.x;
-  const double *k = sorted + (int64_t)b * nb;
-  for (int i = blockIdx.y; i < nm; i += gridDim.y) {
-    const double mi = m[i];
-    double s = 0.0;
-    for (int64_t j = threadIdx.x; j < nb; j += TR_THREADS) s += exp(-k[j] * mi);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < TR_THREADS / 32; ++w) t += red[w];
-      out[(int64_t)b * nm + i] = t / (double)nb;
-    }
-    __syncthreads();
+struct TrConsts {
+  float l1, l2, l3;  // ln2/256 in three parts (l1 with 9 significant bits)
+};
+
+struct TrBin {
+  double k0;     // smallest value
+  double scale;  // 2^F
+  int jz;        // values equal to k0 (they lead the sorted bin)
+  int ju;        // values equal to k0 or below k0 + 2^(F-100) (FP64 terms from jz on)
+  int ok;        // sorted, finite, non-negative
+  int pad;
+};
+
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+  const float h = p + e;
+  return make_float2(h, e - (h - p));
+}
+
+constexpr int TR_TAB = 256;  // 2^{-j/256}, j = 0..255
+
+// 2^{-j/256}, j = 0..255, as float-float pairs (from FP64 exp2)
+__device__ __forceinline__ void tr_table(float2 *tab) {
+  for (int j = threadIdx.x; j < TR_TAB; j += blockDim.x) {
+    const double t = exp2(-(double)j / (double)TR_TAB);
+    const float h = (float)t;
+    tab[j] = make_float2(h, (float)(t - (double)h));
   }
 }
 
+// e^{-d} for d = dh + dl in [0, 87) (|dl| <= ulp(dh)/2), as a pair:
+// d = (n/256) ln 2 - r with |r| <= ln2/512, e^{-d} = 2^{-n/256} e^r,
+// e^r = 1 + r + (r^2/2)(1 + r/3 + r^2/12) (truncation below 1e-18; the
+// bracket's deviation from 1, < 4.6e-4, in FP32).
+__device__ __forceinline__ float2 ff_exp_neg(float dh, float dl, const float2 *tab, const TrConsts &L) {
+  const float n = rintf(dh * 369.32993046757458f);  // 256 / ln 2
+  const int ni = (int)n;
+  // r = n ln2/256 - d: n l1 is exact (l1 has 9 significant bits, n < 2^15)
+  float s, e1;
+  two_sum_f(n * L.l1, -dh, s, e1);
+  const float b = n * L.l2;
+  const float be = fmaf(n, L.l2, -b);
+  float rh, e2;
+  two_sum_f(s, b, rh, e2);
+  float rl = ((e1 + e2) + (be - dl)) + n * L.l3;
+  {
+    const float t = rh + rl;
+    rl = rl - (t - rh);
+    rh = t;
+  }
+  // r^2/2 as a pair, times the bracket
+  const float r2h = rh * rh;
+  const float r2l = fmaf(2.0f * rh, rl, fmaf(rh, rh, -r2h));
+  const float bm1 = rh * fmaf(rh, 1.0f / 12.0f, 1.0f / 3.0f);
+  const float qh = 0.5f * r2h;
+  const float ql = fmaf(qh, bm1, 0.5f * r2l);
+  // E = r + q = e^r - 1
+  float Eh, Ee;
+  two_sum_f(rh, qh, Eh, Ee);
+  float El = Ee + (rl + ql);
+  {
+    const float t = Eh + El;
+    El = El - (t - Eh);
+    Eh = t;
+  }
+  // 2^{-n/256} (1 + E) = T + T E, T = 2^{-(n & 255)/256}, then 2^{-(n >> 8)} (n >> 8 <= 125)
+  const float2 T = tab[ni & (TR_TAB - 1)];
+  const float2 v = ff_add(T, ff_mul(T, make_float2(Eh, El)));
+  const float sc = __int_as_float((127 - (ni >> 8)) << 23);
+  return make_float2(v.x * sc, v.y * sc);
+}
+
+// (sh, sl) += e, renormalized so that |sl| stays within half an ulp of sh
+// (terms near 1 added to a sum near N would otherwise grow sl, and its FP32
+// rounding, with every term)
+__device__ __forceinline__ void tr_acc(float &sh, float &sl, float2 e) {
+  float t, err;
+  two_sum_f(sh, e.x, t, err);
+  sl += err + e.y;
+  sh = t + sl;
+  sl = sl - (sh - t);
+}
+
+// d = D M as a pair (D, M pairs)
+__device__ __forceinline__ float2 ff_prod(float2 D, float2 M) {
+  const float h = D.x * M.x;
+  const float e = fmaf(D.x, M.y, fmaf(D.y, M.x, fmaf(D.x, M.x, -h)));
+  const float t = h + e;
+  return make_float2(t, e - (t - h));
+}
+
+__device__ __forceinline__ float2 split_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// Per bin: k_0, the scale, the counts of equal and of tiny differences, and
+// the differences as scaled pairs D (one CTA per bin).
+__global__ void __launch_bounds__(TR_THREADS)
+    k_trans_prep(const double *__restrict__ sorted, int64_t nb, float2 *__restrict__ D, TrBin *__restrict__ bins) {
+  __shared__ int s_jz, s_ju;
+  const int b = blockIdx.x;
+  const double *k = sorted + (int64_t)b * nb;
+  const double k0 = k[0], kmax = k[nb - 1];
+  if (threadIdx.x == 0) {
+    s_jz = 0;
+    s_ju = 0;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int64_t j = threadIdx.x; j < nb; j += TR_THREADS) {
+    const double v = k[j];
+    bad |= !(v >= 0.0 && isfinite(v)) || (j > 0 && !(k[j - 1] <= v));
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) bins[b] = TrBin{k0, 1.0, 0, 0, 0, 0};
+    return;
+  }
+  const double dmax = kmax - k0;
+  const int F = dmax > 0.0 ? ilogb(dmax) : 0;
+  const double inv = ldexp(1.0, -F);
+  const double tiny = ldexp(1.0, F - 100);
+  int jz = 0, ju = 0;
+  for (int64_t j = threadIdx.x; j < nb; j += TR_THREADS) {
+    const double dj = k[j] - k0;
+    D[(int64_t)b * nb + j] = split_pair(dj * inv);
+    jz += dj == 0.0;
+    ju += dj == 0.0 || dj < tiny;  // (tiny is 0 when 2^(F-100) underflows)
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    jz += __shfl_down_sync(0xffffffffu, jz, o);
+    ju += __shfl_down_sync(0xffffffffu, ju, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_jz, jz);
+    atomicAdd(&s_ju, ju);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) bins[b] = TrBin{k0, ldexp(1.0, F), s_jz, s_ju, 1, 0};
+}
+
+// The sum of the terms of one (bin, m) over the CTA, in a fixed order.
+__device__ __forceinline__ double tr_block_sum(double v, double *red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < TR_THREADS / 32; ++w) t += red[w];
+  return t;  // on thread 0
+}
+
+// One warp per (bin, column mass): a CTA takes one bin and TR_THREADS/32 of
+// its column masses at a time (no CTA barrier); each warp finds its range of
+// terms by a 32-ary search and sums them in a fixed order.
+__global__ void __launch_bounds__(TR_THREADS)
+    k_trans_direct(const double *__restrict__ sorted, int64_t nb, int nm, const double *__restrict__ m,
+                   const float2 *__restrict__ D, const TrBin *__restrict__ bins, TrConsts L,
+                   double *__restrict__ out) {
+  __shared__ float2 tab[TR_TAB];
+  tr_table(tab);
+  __syncthreads();
+  const int b = blockIdx.x, lane = threadIdx.x & 31;
+  const double *k = sorted + (int64_t)b * nb;
+  const float2 *Db = D + (int64_t)b * nb;
+  const TrBin B = bins[b];
+  constexpr int WPB = TR_THREADS / 32;
+  for (int i = blockIdx.y * WPB + (threadIdx.x >> 5); i < nm; i += gridDim.y * WPB) {  // warp-uniform
+    const double mi = m[i];
+    double res = 0.0;
+    if (!B.ok) {  // the plain FP64 sum
+      double s = 0.0;
+      for (int64_t j = lane; j < nb; j += 32) s += exp(-k[j] * mi);
+      res = warp_sum(s) / (double)nb;
+    } else {
+      const double E0 = exp(-(B.k0 * mi));
+      if (E0 > 0.0) {  // else every term underflows, as e^{-k_0 m} does
+        // jmax: the first j >= ju with (k_j - k_0) m >= 87 (nb if none), the
+        // lanes probing 32 evenly spaced places of [lo, hi) a round
+        int64_t lo = B.ju, hi = nb;
+        while (hi > lo) {
+          const int64_t span = hi - lo;
+          const int64_t step = (span + 31) >> 5;
+          const int64_t p = lo + (int64_t)lane * step;
+          const bool past = p < hi && (k[p] - B.k0) * mi >= TR_DMAX;
+          const unsigned bal = __ballot_sync(0xffffffffu, past);
+          if (step == 1) {  // every place probed: the first past one, or hi
+            hi = bal ? lo + __ffs(bal) - 1 : hi;
+            break;
+          }
+          // the first lane past (the probes increase, so all later valid ones are past too);
+          // none past: the answer lies after the last valid probe
+          const int64_t last = (span - 1) / step;  // lanes 0..last probe inside [lo, hi)
+          if (bal) {
+            const int f = __ffs(bal) - 1;
+            const int64_t nhi = lo + (int64_t)f * step;
+            lo = f > 0 ? lo + (int64_t)(f - 1) * step + 1 : lo;
+            hi = nhi;
+          } else {
+            lo = lo + last * step + 1;
+          }
+        }
+        const int64_t jmax = hi;
+        double pd = 0.0;  // tiny differences, FP64
+        for (int64_t j = B.jz + lane; j < min((int64_t)B.ju, jmax); j += 32) pd += exp(-((k[j] - B.k0) * mi));
+        float sh = 0.0f, sl = 0.0f;
+        if (jmax > B.ju) {  // then m 2^F < 87 2^100 (a pair)
+          const float2 M = split_pair(mi * B.scale);
+          // two terms a lane per pass (independent exponentials side by side)
+          int64_t j = B.ju + lane;
+          for (; j + 32 < jmax; j += 64) {
+            const float2 d0 = ff_prod(Db[j], M), d1 = ff_prod(Db[j + 32], M);
+            const float2 e0 = ff_exp_neg(fminf(d0.x, 86.0f), d0.y, tab, L);
+            const float2 e1 = ff_exp_neg(fminf(d1.x, 86.0f), d1.y, tab, L);
+            if (d0.x < (float)TR_DMAX) tr_acc(sh, sl, e0);
+            if (d1.x < (float)TR_DMAX) tr_acc(sh, sl, e1);
+          }
+          if (j < jmax) {
+            const float2 d = ff_prod(Db[j], M);
+            if (d.x < (float)TR_DMAX) tr_acc(sh, sl, ff_exp_neg(d.x, d.y, tab, L));
+          }
+        }
+        const double t = warp_sum((double)sh + (double)sl + pd);
+        res = E0 * ((double)B.jz + t) / (double)nb;
+      }
+    }
+    if (lane == 0) out[(int64_t)b * nm + i] = res;
+  }
+}
+
+// k(g) of a bin from its fit at g_j = (j + 1/2)/ng, FP64
+__device__ __forceinline__ double tr_kfit(const double *c, int ncheb, int j, int ng) {
+  const double t = 2.0 * (((double)j + 0.5) / (double)ng) - 1.0;
+  double tkm1 = 1.0, tk = t, v = c[0];
+  if (ncheb > 1) v += c[1] * t;
+  for (int q = 2; q < ncheb; ++q) {
+    const double tn = 2.0 * t * tk - tkm1;
+    v += c[q] * tn;
+    tkm1 = tk;
+    tk = tn;
+  }
+  return exp(v);
+}
+
+// One CTA per (bin, block of column masses), one column mass a thread, the
+// fit's ng values of k (and their pairs) in shared memory.  The values are
+// not sorted, so every point is visited; terms with d >= 87 are skipped.
 __global__ void __launch_bounds__(TR_THREADS)
     k_trans_fit(const double *__restrict__ coef, int ncheb, int ng, int nm, const double *__restrict__ m,
+                TrConsts L, double *__restrict__ out) {
+  extern __shared__ double kfit[];  // ng values, then ng pairs (a negative pair: FP64 term)
+  float2 *Dg = reinterpret_cast<float2 *>(kfit + ng);
+  __shared__ float2 tab[TR_TAB];
+  __shared__ double rmin[TR_THREADS / 32], rmax[TR_THREADS / 32];
+  tr_table(tab);
+  const int b = blockIdx.x;
+  const double *c = coef + (int64_t)b * ncheb;
+  double vmin = INFINITY, vmax = 0.0;
+  bool bad = false;
+  for (int j = threadIdx.x; j < ng; j += TR_THREADS) {
+    const double v = tr_kfit(c, ncheb, j, ng);
+    kfit[j] = v;
+    bad |= !isfinite(v);
+    vmin = fmin(vmin, v);
+    vmax = fmax(vmax, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vmin = fmin(vmin, __shfl_down_sync(0xffffffffu, vmin, o));
+    vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rmin[threadIdx.x >> 5] = vmin;
+    rmax[threadIdx.x >> 5] = vmax;
+  }
+  bad = __syncthreads_or(bad);
+  vmin = INFINITY;
+  vmax = 0.0;
+  for (int w = 0; w < TR_THREADS / 32; ++w) {
+    vmin = fmin(vmin, rmin[w]);
+    vmax = fmax(vmax, rmax[w]);
+  }
+  const double dmax = vmax - vmin;
+  const int F = dmax > 0.0 ? ilogb(dmax) : 0;
+  const double inv = ldexp(1.0, -F), tiny = ldexp(1.0, F - 100), scale = ldexp(1.0, F);
+  if (!bad)
+    for (int j = threadIdx.x; j < ng; j += TR_THREADS) {
+      const double dj = kfit[j] - vmin;
+      Dg[j] = (dj == 0.0 || dj >= tiny) ? split_pair(dj * inv) : make_float2(-1.0f, 0.0f);
+    }
+  __syncthreads();
+  for (int i = blockIdx.y * TR_THREADS + threadIdx.x; i < nm; i += gridDim.y * TR_THREADS) {
+    const double mi = m[i];
+    double res;
+    if (bad) {  // the plain FP64 sum
+      double s = 0.0;
+      for (int j = 0; j < ng; ++j) s += exp(-kfit[j] * mi);
+      res = s / (double)ng;
+    } else {
+      const double E0 = exp(-(vmin * mi));
+      res = 0.0;
+      if (E0 > 0.0) {
+        const double Md = mi * scale;
+        const bool pairs = Md < 0x1p107;  // else every pair term has d >= 128
+        const float2 M = split_pair(pairs ? Md : 0.0);
+        float sh = 0.0f, sl = 0.0f;
+        double pd = 0.0;
+        for (int j = 0; j < ng; ++j) {
+          const float2 Dj = Dg[j];
+          if (Dj.x < 0.0f) {
+            pd += exp(-((kfit[j] - vmin) * mi));
+          } else if (pairs) {
+            const float2 d = ff_prod(Dj, M);
+            if (d.x < (float)TR_DMAX) {
+              tr_acc(sh, sl, ff_exp_neg(d.x, d.y, tab, L));
+            }
+          }
+        }
+        res = E0 * ((double)sh + (double)sl + pd) / (double)ng;
+      }
+    }
+    out[(int64_t)b * nm + i] = res;
+  }
+}
+
+// The plain FP64 fit transmission, for ng too large for k_trans_fit's shared
+// memory (16 B a point).
+__global__ void __launch_bounds__(TR_THREADS)
+    k_trans_fit64(const double *__restrict__ coef, int ncheb, int ng, int nm, const double *__restrict__ m,
                 double *__restrict__ out) {
   extern __shared__ double kfit[];  // ng values
   const int b = blockIdx.x;
@@ -1386,25 +1708,60 @@ __global__ void __launch_bounds__(TR_THREADS)
   }
 }
 
+// ln2/256 in three parts, the first with 9 significant bits (so that n l1 is
+// exact for n < 2^15)
+static TrConsts tr_consts() {
+  const double L = 0.69314718055994530941723212145817657 / 256.0;
+  float l1 = (float)L;
+  uint32_t u;
+  memcpy(&u, &l1, 4);
+  u &= 0xFFFF8000u;
+  memcpy(&l1, &u, 4);
+  const float l2 = (float)(L - (double)l1);
+  const float l3 = (float)(L - (double)l1 - (double)l2);
+  return TrConsts{l1, l2, l3};
+}
+
+size_t trans_pair_bytes(int nbins, int64_t nb) { return (size_t)nbins * (size_t)nb * sizeof(float2); }
+size_t trans_bin_bytes(int nbins) { return (size_t)nbins * sizeof(TrBin); }
+
 cudaError_t launch_transmission(helk_ctx *c, int nbins, int64_t nb, const double *sorted,
                                 const double *coef, int ncheb, int ng, int nm, const double *m_dev,
                                 double *direct, double *fit) {
+  const TrConsts L = tr_consts();
   if (sorted && direct) {
-    dim3 grid(nbins, std::min(nm, 64));
+    float2 *D = reinterpret_cast<float2 *>(c->tr_pairs);
+    TrBin *bins = reinterpret_cast<TrBin *>(c->tr_bins);
     ++c->launches;
-    k_trans_direct<<<grid, TR_THREADS, 0, c->stream>>>(sorted, nb, nm, m_dev, direct);
+    k_trans_prep<<<nbins, TR_THREADS, 0, c->stream>>>(sorted, nb, D, bins);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid(nbins, std::max(1, std::min(8, (nm + TR_THREADS / 32 - 1) / (TR_THREADS / 32))));
+    ++c->launches;
+    k_trans_direct<<<grid, TR_THREADS, 0, c->stream>>>(sorted, nb, nm, m_dev, D, bins, L, direct);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (coef && fit) {
-    const size_t smem = (size_t)ng * 8;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_trans_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
     dim3 grid(nbins, (nm + TR_THREADS - 1) / TR_THREADS);
-    ++c->launches;
-    k_trans_fit<<<grid, TR_THREADS, smem, c->stream>>>(coef, ncheb, ng, nm, m_dev, fit);
+    const size_t smem = (size_t)ng * (sizeof(double) + sizeof(float2));
+    if (smem + 2048 <= (size_t)c->max_smem_optin) {
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_trans_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      ++c->launches;
+      k_trans_fit<<<grid, TR_THREADS, smem, c->stream>>>(coef, ncheb, ng, nm, m_dev, L, fit);
+    } else {
+      const size_t smem64 = (size_t)ng * sizeof(double);
+      if (smem64 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_trans_fit64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem64);
+        if (e != cudaSuccess) return e;
+      }
+      ++c->launches;
+      k_trans_fit64<<<grid, TR_THREADS, smem64, c->stream>>>(coef, ncheb, ng, nm, m_dev, fit);
+    }
     return cudaGetLastError();
   }
   return cudaSuccess;
