@@ -299,8 +299,12 @@ struct __align__(16) WarpLine {
   float q0, q1, q2, q3;  // GH1: P1; GH3S: g0, g1, g2 (Gh3Series); rest: P1, or GH3's C, c3, c45, c2 (Gh3Line)
 };
 
-// Whole-span lines [t, t1) of one kind: GH1 (4 instructions an evaluation)
-// or GH3 by its series (6), u stepped from the base slot.
+// Whole-span lines [t, t1) of one kind: GH1 or GH3 by its series, u stepped
+// from the base slot.  GH1 takes one reciprocal for two slots, 1/r_a^2 =
+// r_b^2 / (r_a^2 r_b^2) (5 instructions and half a reciprocal an evaluation
+// instead of 4 and one: the MUFU unit, at 16 reciprocals a clock per SM, is
+// the co-bound of this loop mix); the series keeps one reciprocal a slot (6
+// instructions), where pairing would make the issue count the bound.
 template <int NSLOT, bool FWD, bool GH3S>
 __device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, float lanef, int &ngroup,
                                            float (&sum)[NSLOT], float (&comp)[NSLOT], float (&part)[NSLOT]) {
@@ -323,9 +327,17 @@ __device__ __forceinline__ void span_lines(const WarpLine *wl, int t, int t1, fl
       } else {
         const float P1 = W.q0;
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-          const float u = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
-          part[k] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[k]);
+        for (int k = 0; k + 1 < NSLOT; k += 2) {
+          const float u0 = fmaf(FWD ? (float)k : (float)(k - (NSLOT - 1)), h, ub);
+          const float u1 = fmaf(FWD ? (float)(k + 1) : (float)(k + 1 - (NSLOT - 1)), h, ub);
+          const float ra = fmaf(u0, u0, a2), rb = fmaf(u1, u1, a2);
+          const float rr = fast_rcp(ra * rb);
+          part[k] = fmaf(P1 * rb, rr, part[k]);
+          part[k + 1] = fmaf(P1 * ra, rr, part[k + 1]);
+        }
+        if (NSLOT & 1) {
+          const float u = fmaf(FWD ? (float)(NSLOT - 1) : 0.0f, h, ub);
+          part[NSLOT - 1] = fmaf(P1, fast_rcp(fmaf(u, u, a2)), part[NSLOT - 1]);
         }
       }
     }
@@ -476,7 +488,9 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           r.nphi = nphi;
           r.a2 = a2;
           const bool series = cls == CLS_GH3 && Gh3Series::holds(r2near, a2);
-          if (full && (cls == CLS_GH1 || series) && (dlo >= 0 || dhi <= 0)) {
+          // (GH1 spans reach r^2 < 1e18 only: the paired reciprocals' product
+          // of two r^2 stays inside the FP32 range; farther spans run as the rest)
+          if (full && ((cls == CLS_GH1 && r2far < 1.0e18f) || series) && (dlo >= 0 || dhi <= 0)) {
             const bool fwd = dlo >= 0;
             r.kind = (cls == CLS_GH1 ? KIND_GH1_FWD : KIND_GH3S_FWD) + (fwd ? 0 : 1);
             r.d0 = (float)(fwd ? dlo : dhi - 31);  // lane 0 at slot 0 or NSLOT - 1
