@@ -405,6 +405,10 @@ cudaError_t launch_lineprep(helk_ctx *c, int n_cond, const CondArgs *single, dou
 // decades below it); the centre as the integer grid index c plus the FP32
 // offset phi = (nu0' - nu_c) ku, so that u_i = (i - c) beta - phi keeps full
 // relative precision near the line centre.
+// the 3-node GH factor over S' a: (sqrt(pi)/6)/pi, as one constant (one FP64
+// multiplication a line instead of a division)
+constexpr double P3_FACTOR = SQRTPI / 6.0 / PI;
+
 __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, double nu_min, double dnu, int64_t ngrid,
                          const double *__restrict__ ckey, CondStats *cst_all, LineRec32 *__restrict__ r32_all,
                          int2 *__restrict__ core_all, int32_t *__restrict__ ckey32, int *err_flags,
@@ -422,8 +426,11 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const LineRec64 r = r64[l];
-    const double key = ckey[l];
-    if (cond == 0) ckey32[l] = (int32_t)fmin(fmax(key, -2147483647.0), 2147483647.0);
+    // the reference index is an integer below 2^53 in magnitude: integer
+    // operations from here on (the FP64 unit bounds this kernel)
+    const long long key = (long long)ckey[l];
+    const int k32 = (int)min(max(key, -2147483647ll), 2147483647ll);
+    if (cond == 0) ckey32[l] = k32;
     LineRec32 q;
     // any integer within a step of the centre serves as c (phi takes the
     // rest), so a product by 1/dnu replaces the division
@@ -444,7 +451,7 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     q.a2 = (float)r.a2;
     const double sp = r.Sp * pow2mE;
     q.P1 = (float)(sp * r.a * INV_SQRTPI);
-    q.P3 = (float)(sp * r.a * (SQRTPI / 6.0) / PI);
+    q.P3 = (float)(sp * r.a * P3_FACTOR);
     q.Sp = (float)sp;
     if (q.a < 10.0f) {  // Algorithm 916 per-line factors, in FP32
       q.erfcx_a = erfcxf(q.a);
@@ -473,16 +480,18 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
       const float reach = clamped ? 10.001f - fabsf(q.phi_k) : 10.001f + fabsf(q.phi_k);
       if (reach > 0.0f) {
         // an upper bound (FP32 quotient, rounding covered by the margin of 2)
-        const double dmax = (double)ceilf(reach / q.beta) + 2.0;
+        const float dmaxf = ceilf(reach / q.beta) + 2.0f;
         // Both Voigt kernels take i - c exactly in FP32 only within 2^24
         // points of c, so a core must end within 2^23 points (beta above
         // ~1.2e-6: a Doppler width below ~7e5 grid steps); else the call is
         // reported as unsupported by the FP32 form.
-        if (dmax >= 8388608.0) atomicOr(err_flags, ERRF_F32_RANGE);
-        const double clo = fmax((double)q.ilo, (double)q.c - dmax), chi = fmin((double)q.ihi, (double)q.c + dmax);
+        if (dmaxf >= 8388608.0f) atomicOr(err_flags, ERRF_F32_RANGE);
+        const long long dmax = (long long)fminf(dmaxf, 4.0e9f);
+        const long long clo = max((long long)q.ilo, (long long)q.c - dmax);
+        const long long chi = min((long long)q.ihi, (long long)q.c + dmax);
         if (clo <= chi) {
-          const double w = fmax(key - clo, chi - key);
-          line_w1 = (int)fmin(w + 1.0, 2.0e9);
+          const long long w = max(key - clo, chi - key);
+          line_w1 = (int)min(w + 1, 2000000000ll);
           cw1 = max(cw1, line_w1);
           core = make_int2((int)clo, (int)chi);
         }
@@ -493,7 +502,6 @@ __global__ void k_pack32(int64_t n, const LineRec64 *__restrict__ r64_all, doubl
     // CORE_BLK_PTS grid points (the core kernel's candidate window): the
     // list is ordered by the index, so the lanes of a warp mostly share a
     // block and one atomic per block and warp suffices.
-    const int k32 = (int)fmin(fmax(key, -2147483647.0), 2147483647.0);
     const int blk = min(max(k32 >> 12, 0), nblk - 1);  // CORE_BLK_PTS = 2^12
     const unsigned peers = __match_any_sync(__activemask(), blk);
     const int wblk = __reduce_max_sync(peers, line_w1);
