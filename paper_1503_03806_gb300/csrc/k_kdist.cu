@@ -1211,13 +1211,23 @@ __global__ void __launch_bounds__(KF_THREADS)
     __syncthreads();   // and everyone's
     const int ncol = min(KF_COLS, c1 - cc);
     if (bin < nbins) {
-      for (int b = 0; b < (ncol >> 5); ++b) {
-        const float4 l = Lst(st)[w * KF_COLS + 32 * b + lane];  // zero past nh
-        const float2 Lp = make_float2(l.x, l.y), Lm = make_float2(l.z, l.w);
-        const float2 *pb = Pst(st) + b * ncheb * 32 + lane;
+      if (ncheb == NC) {  // every accumulator used: no per-coefficient test
+        for (int b = 0; b < (ncol >> 5); ++b) {
+          const float4 l = Lst(st)[w * KF_COLS + 32 * b + lane];  // zero past nh
+          const float2 Lp = make_float2(l.x, l.y), Lm = make_float2(l.z, l.w);
+          const float2 *pb = Pst(st) + b * NC * 32 + lane;
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
-          if (k < ncheb) dfma_acc(sh[k], sl[k], pb[k * 32], (k & 1) ? Lm : Lp);
+          for (int k = 0; k < NC; ++k) dfma_acc(sh[k], sl[k], pb[k * 32], (k & 1) ? Lm : Lp);
+        }
+      } else {
+        for (int b = 0; b < (ncol >> 5); ++b) {
+          const float4 l = Lst(st)[w * KF_COLS + 32 * b + lane];  // zero past nh
+          const float2 Lp = make_float2(l.x, l.y), Lm = make_float2(l.z, l.w);
+          const float2 *pb = Pst(st) + b * ncheb * 32 + lane;
+#pragma unroll
+          for (int k = 0; k < NC; ++k)
+            if (k < ncheb) dfma_acc(sh[k], sl[k], pb[k * 32], (k & 1) ? Lm : Lp);
+        }
       }
     }
     __syncthreads();  // the stage is refilled two chunks on
