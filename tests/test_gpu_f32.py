@@ -95,9 +95,11 @@ def test_medium_workload_whole_bins(ctx):
     check_binned(k[idx], ko, len(bins), "medium workload bins %s" % bins)
 
 
-@pytest.mark.parametrize("P,ngrid", [(1e-7, 2048 + 5), (0.02, 1), (100.0, 33), (3000.0, 2048 + 5)])
+@pytest.mark.parametrize("P,ngrid", [(0.0, 2048 + 5), (1e-7, 2048 + 5), (0.02, 1), (100.0, 33),
+                                     (3000.0, 2048 + 5)])
 def test_pressure_extremes_and_tiny_grids(ctx, P, ngrid):
-    # 1e-7 atm: Doppler cores, no wings to speak of; 0.02 atm: a < 10, cores
+    # 0 atm: a = 0, the Gaussian limit (Algorithm 916 with y = 0 in the cores,
+    # zero wings); 1e-7 atm: Doppler cores, no wings to speak of; 0.02 atm: a < 10, cores
     # beside GH3 wings; 100 and 3000 atm: a^2 >= 1e6 for most lines, so whole
     # spans that hold the line centre are GH1 (or GH3) without a core; grids
     # of 1, 33 and 2053 points (one ragged tile)
