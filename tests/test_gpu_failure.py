@@ -54,3 +54,37 @@ def test_selftest_limit_is_checked():
         assert helk.lib.helk_selftest_timeout(ctx.h, 10 * 1000 * 1000 + 1) == helk.HELK_ERR_INVALID_ARG
     finally:
         ctx.close()
+
+
+def test_oversized_request_reports_oom_and_context_survives():
+    # 160 conditions of a 2^31 - 4097-point grid into the library's own
+    # opacity buffer: 2.75 TB, beyond any device.  The buffer's cudaMalloc
+    # fails (an ordinary error return, no GPU fault), the call returns
+    # HELK_ERR_OOM with its message, and the same context then runs a
+    # normal call.
+    import ctypes
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_03806_gb300 import build
+    build.build()
+    from paper_1503_03806_gb300 import helk
+    ctx = helk.Context(0)
+    try:
+        ctx.upload(synth.random_lines(50, 702, 10.0, 20.0))
+        n_cond, n = 160, 2 ** 31 - 4097
+        T = np.full(n_cond, 1500.0)
+        P = np.full(n_cond, 1.0)
+        g = helk.helk_grid(0.0, 0.01, n)
+        o = helk.helk_opts(helk.HELK_PREC_F32_KAHAN, 0, 1.0, 1.0, 0, 0)
+        st = helk.lib.helk_opacity_batch(ctx.h, n_cond, T.ctypes.data_as(helk._P), P.ctypes.data_as(helk._P),
+                                         None, 18.0, ctypes.byref(helk._cut(("abs", 1.0))), ctypes.byref(g),
+                                         ctypes.byref(o), None)
+        assert st == helk.HELK_ERR_OOM, st
+        assert "out of device memory" in helk.helk_last_error(ctx.h)
+        ctx.sync()
+        k = ctx.opacity(1500.0, 1.0, 18.0, ("abs", 2.0), (10.0, 0.01, 1000),
+                        precision=helk.HELK_PREC_F32_KAHAN)
+        ctx.sync()
+        assert np.isfinite(k.cpu().numpy()).all() and k.sum().item() > 0
+    finally:
+        ctx.close()
