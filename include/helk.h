@@ -126,27 +126,33 @@ typedef struct {
 } helk_opts;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream`
- * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * (a cudaStream_t; NULL = the legacy default stream).  No counterpart in
+ * the paper (context plumbing, as are helk_destroy, helk_last_error,
+ * helk_set_stream and helk_sync).  *out receives the
  * context; release it with helk_destroy. */
 helk_status helk_create(helk_ctx **out, int device, void *stream);
 
-/* Free the context and every device buffer it owns (synchronises first). */
+/* Free the context and every device buffer it owns (synchronises first).
+ * No counterpart in the paper. */
 void helk_destroy(helk_ctx *ctx);
 
 /* Last error message of this context ("" if none).  Valid until the next
- * call on the context. */
+ * call on the context.  No counterpart in the paper. */
 const char *helk_last_error(const helk_ctx *ctx);
 
-/* Change the stream later work is enqueued on. */
+/* Change the stream later work is enqueued on.  No counterpart in the
+ * paper. */
 helk_status helk_set_stream(helk_ctx *ctx, void *stream);
 
 /* Wait for all work of the context and report kernel-side errors, each
  * once (the context stays usable): a bounded wait that gave up
  * (HELK_ERR_TIMEOUT); an FP32-form call outside that form's range
- * (HELK_ERR_UNSUPPORTED, see HELK_PREC_F32_KAHAN). */
+ * (HELK_ERR_UNSUPPORTED, see HELK_PREC_F32_KAHAN).  No counterpart in the
+ * paper. */
 helk_status helk_sync(helk_ctx *ctx);
 
-/* Failure-detection self-test: launches a kernel whose bounded wait, the
+/* Failure-detection self-test (no counterpart in the paper): launches a
+ * kernel whose bounded wait, the
  * one every staged copy of the Voigt kernels uses, waits on a barrier that
  * nothing completes.  The wait is bounded in time, by the GPU's global timer:
  * it gives up after limit_us microseconds (1 .. 1e7; the Voigt kernels use
@@ -154,8 +160,9 @@ helk_status helk_sync(helk_ctx *ctx);
  * HELK_ERR_TIMEOUT.  No fault, no hang. */
 helk_status helk_selftest_timeout(helk_ctx *ctx, int32_t limit_us);
 
-/* Upload (copy) a line list into context-owned device memory and order it
- * by nu0 (stable), replacing any previous list.  `on_device` = 0: the
+/* Upload (copy) a line list -- the per-line parameters of Sec. 2.3 -- into
+ * context-owned device memory and order it by nu0 (stable), replacing any
+ * previous list.  `on_device` = 0: the
  * pointers in *lines are host memory; 1: device memory.  n >= 0.
  * Validation of values runs on the device and is reported here (the call
  * synchronises the stream). */
@@ -199,19 +206,22 @@ helk_status helk_opacity_batch(helk_ctx *ctx, int32_t n_cond, const double *T,
                                double *kappa_out);
 
 /* Line-record budget of one chunk of helk_opacity_batch, in bytes (0: the
- * default, 64 GiB).  A chunk always holds at least one condition, so a
+ * default, 64 GiB); no counterpart in the paper.  A chunk always holds at least one condition, so a
  * budget below one condition's records runs the conditions one by one.
  * Host-only. */
 helk_status helk_set_batch_budget(helk_ctx *ctx, int64_t bytes);
 
-/* Evaluation counts of the first n_cond conditions of the last opacity call
+/* Evaluation counts (of the Sec. 2.4 methods; a measurement with no
+ * counterpart in the paper) of the first n_cond conditions of the last
+ * opacity call
  * (n_evals[k]; region_counts[4k..4k+3] as in helk_opacity_stats when that call
  * counted regions, else pass NULL).  Synchronises. */
 helk_status helk_opacity_batch_stats(helk_ctx *ctx, int32_t n_cond,
                                      int64_t *n_evals, int64_t *region_counts);
 
-/* Statistics of the last helk_opacity: number of (line, grid point) Voigt
- * evaluations and, if region_counts != NULL (4 entries; the last opacity
+/* Statistics of the last helk_opacity (a measurement with no counterpart
+ * in the paper): number of (line, grid point) Voigt evaluations within the
+ * Sec. 2.4 windows and, if region_counts != NULL (4 entries; the last opacity
  * must have run with count_regions), how many fell in each method
  * [Algorithm 916, GH3, GH1] plus the number of Algorithm 916 series terms
  * summed.  Synchronises. */
@@ -245,7 +255,9 @@ helk_status helk_kdist(helk_ctx *ctx, const double *kappa, int64_t n,
                        double *coeffs, double *mean, int32_t out_on_host,
                        double *kg_out);
 
-/* Autotuner of the Voigt kernel's shape.  A shape is one built
+/* Autotuner of the Voigt kernel's shape (no counterpart in the paper; the
+ * helk_tile_* calls and helk_set_tile below belong to it).  A shape is one
+ * built
  * configuration of a precision's persistent Voigt kernel: the tile (grid
  * points per CTA tile), the warps per CTA and the candidate lines per
  * pipeline stage; it is named by a shape code (helk_tile_shape decodes it).
@@ -261,20 +273,23 @@ helk_status helk_autotune(helk_ctx *ctx, double T, double P_atm,
                           const helk_grid *grid, const helk_opts *opts,
                           int32_t *tile_out);
 
-/* The shape codes of a precision that the autotuner times (FP32: the
+/* The shape codes of a precision that the autotuner times (no counterpart
+ * in the paper; FP32: the
  * 1-based positions of its built shapes; FP64: slots per warp, 4, 6, 8):
  * writes up to `max` of them to out (host memory) and returns how many there
  * are.  No device work; returns 0 for an unknown precision or out == NULL. */
 int32_t helk_tile_candidates(int32_t precision, int32_t *out, int32_t max);
 
-/* Decodes a shape code of `precision`: points per CTA tile, warps per CTA
+/* Decodes a shape code of `precision` (no counterpart in the paper):
+ * points per CTA tile, warps per CTA
  * and candidate lines per pipeline stage (each output optional, host
  * memory).  HELK_ERR_INVALID_ARG for an unknown precision or code.  No
  * device work. */
 helk_status helk_tile_shape(int32_t precision, int32_t code, int32_t *points,
                             int32_t *warps, int32_t *lines_per_stage);
 
-/* Fixes the Voigt kernel shape of `precision` for grids of n points (what
+/* Fixes the Voigt kernel shape of `precision` (no counterpart in the paper)
+ * for grids of n points (what
  * helk_autotune would store), or, with tile == 0, returns to the built-in
  * choice.  tile must be one of helk_tile_candidates(precision); anything
  * else returns HELK_ERR_INVALID_ARG.  The shape changes no FP64 result and
@@ -283,13 +298,14 @@ helk_status helk_tile_shape(int32_t precision, int32_t code, int32_t *points,
 helk_status helk_set_tile(helk_ctx *ctx, int32_t precision, int64_t n, int32_t tile);
 
 /* Number of CUDA kernels the context has launched since it was created
- * (tracing: a caller can bracket a region with two calls).  Launches that a
+ * (tracing, no counterpart in the paper: a caller can bracket a region with two calls).  Launches that a
  * replayed CUDA graph makes (helk_opacity_batch after its first call with
  * given sizes) are counted when the graph is captured, not at each replay.
  * Host-only; returns -1 for ctx == NULL. */
 int64_t helk_launch_count(const helk_ctx *ctx);
 
-/* Stage timing (tracing).  With profiling on, the library records a CUDA
+/* Stage timing (tracing: the paper's per-stage breakdown of Sec. 3.5).
+ * With profiling on, the library records a CUDA
  * event pair on the context stream around each stage it launches:
  *   HELK_STAGE_LINEPREP  line preparation and the tile map (Sec. 2.3-2.4)
  *   HELK_STAGE_VOIGT     the Voigt/opacity kernel (Sec. 2.3-2.4)
@@ -317,36 +333,43 @@ helk_status helk_stage_times(helk_ctx *ctx, double *ms, int64_t *count);
  * the network cell by cell (helk_surrogate_validate), and only validated
  * cells are routed to it (helk_opts.surrogate).
  * ------------------------------------------------------------------- */
-/* (Re)initialise the network with seeded normal weights, zero biases. */
+/* (Re)initialise the network with seeded normal weights, zero biases.
+ * Surrogate calls have no counterpart in the paper (see above). */
 helk_status helk_surrogate_init(helk_ctx *ctx, uint64_t seed);
-/* Copy the parameters to get_host (8577 floats) and/or replace them from
+/* (Surrogate, no counterpart in the paper.)  Copy the parameters to
+ * get_host (8577 floats) and/or replace them from
  * set_host (resets the optimiser state); either may be NULL.  Synchronises. */
 helk_status helk_surrogate_params(helk_ctx *ctx, float *get_host,
                                   const float *set_host);
-/* n seeded samples of the core region (|x| asinh-uniform in [0, 10], y
+/* (Surrogate, no counterpart in the paper.)  n seeded samples of the
+ * Sec. 2.4 core region (|x| asinh-uniform in [0, 10], y
  * log-uniform in [1e-4, 10), x^2 + y^2 < 100): features feat[2i], feat[2i+1],
  * target ln(K/K_ref) with K by FP64 Algorithm 916, and optionally x, y.
  * Device pointers. */
 helk_status helk_surrogate_samples(helk_ctx *ctx, int64_t n, uint64_t seed,
                                    float *feat, float *target, double *x,
                                    double *y);
-/* Gradient of the mean squared residual error over n samples (device
+/* (Surrogate, no counterpart in the paper.)  Gradient of the mean squared
+ * residual error over n samples (device
  * feat/target) at the current parameters, to grad_host (8577 floats) and
  * the loss to loss_host; no update.  Synchronises. */
 helk_status helk_surrogate_grad(helk_ctx *ctx, int64_t n, const float *feat,
                                 const float *target, float *grad_host,
                                 double *loss_host);
-/* Train with Adam on n_samples fresh samples (seed) for `epochs` passes in
+/* (Surrogate, no counterpart in the paper.)  Train with Adam on n_samples
+ * fresh samples (seed) for `epochs` passes in
  * minibatches of `batch` (>= 128), learning rate lr with cosine decay to 1 %.
  * final_loss (host, optional): mean squared residual error of the last
  * epoch.  Synchronises after every epoch. */
 helk_status helk_surrogate_train(helk_ctx *ctx, int64_t n_samples,
                                  uint64_t seed, int32_t epochs, int32_t batch,
                                  double lr, double *final_loss);
-/* K(x_i, y_i) by the network for n points (device arrays). */
+/* (Surrogate, no counterpart in the paper.)  K(x_i, y_i) by the network for
+ * n points (device arrays). */
 helk_status helk_surrogate_eval(helk_ctx *ctx, int64_t n, const double *x,
                                 const double *y, double *k);
-/* Held-out check on an nx x ny partition of the feature square with
+/* (Surrogate, no counterpart in the paper.)  Held-out check on an nx x ny
+ * partition of the feature square with
  * per_cell^2 points at sub-cell centres (points with x^2 + y^2 >= 100 are
  * skipped): a cell is validated when every checked point has
  * |K_net - K_916| <= tol K_916.  Writes mask_host[cy*nx + cx] (0/1) and
