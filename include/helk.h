@@ -299,8 +299,9 @@ helk_status helk_set_tile(helk_ctx *ctx, int32_t precision, int64_t n, int32_t t
 
 /* Number of CUDA kernels the context has launched since it was created
  * (tracing, no counterpart in the paper: a caller can bracket a region
- * with two calls).  Launches that a replayed CUDA graph makes (helk_opacity_batch after its first call with
- * given sizes) are counted when the graph is captured, not at each replay.
+ * with two calls).  Launches that a replayed CUDA graph makes
+ * (helk_opacity_batch after its first call with given sizes) are counted
+ * when the graph is captured, not at each replay.
  * Host-only; returns -1 for ctx == NULL. */
 int64_t helk_launch_count(const helk_ctx *ctx);
 
