@@ -103,3 +103,26 @@ def test_oracle_and_product_share_nothing():
         text = open(f).read()
         assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
         assert "liboracle" not in text and "helk_oracle" not in text, f
+
+
+def test_static_kdist_limits_are_checked_before_any_gpu_work(helk):
+    # helk_kdist_static rejects what its fixed scratch cannot hold -- bins
+    # above 12288 points, more than 32 coefficients -- and malformed sizes,
+    # before it touches a device (the pointers are never dereferenced here)
+    lib = helk.lib
+    fake = ctypes.c_void_p(0x1000)
+    bad = [
+        (2 * 12289, 2, 20, 1e-250),   # 12289 points a bin: above the maximum
+        (100, 1, 33, 1e-250),         # 33 coefficients
+        (100, 1, 0, 1e-250),          # no coefficient
+        (101, 2, 20, 1e-250),         # n not a multiple of nbins
+        (100, 10, 20, 1e-250),        # ncheb > N_b
+        (100, 1, 20, 0.0),            # floor must be > 0
+        (100, 1, 20, float("nan")),
+        (0, 1, 20, 1e-250),
+    ]
+    for n, nbins, ncheb, floor in bad:
+        st = lib.helk_kdist_static(fake, n, nbins, ncheb, floor, fake, None, None, None)
+        assert st == helk.HELK_ERR_INVALID_ARG, (n, nbins, ncheb, floor)
+    assert lib.helk_kdist_static(None, 100, 1, 20, 1e-250, fake, None, None, None) == helk.HELK_ERR_INVALID_ARG
+    assert lib.helk_kdist_static(fake, 100, 1, 20, 1e-250, None, None, None, None) == helk.HELK_ERR_INVALID_ARG
